@@ -1,0 +1,270 @@
+/*
+ * amgsym.h -- C ABI of the symmetry-reduced AMG-PCG Poisson solver.
+ *
+ * Method: A. Alsalti-Baldellou, C. Janna, X. Alvarez-Farre, F. X. Trias,
+ * "A multigrid reduction framework for domains with symmetries" (arXiv 2407.05930).
+ *
+ *   Sec. 2, eq. "fields_struct", Fig. "1d_case": mirrored ordering of the unknowns.
+ *   Sec. 2, eq. "struct_2sym": with s reflection symmetries the operator has
+ *       2^s x 2^s blocks, block (p, q) = H_{p XOR q} (0-based copies).
+ *   Sec. 2, eq. "split_s": H = I_{2^s} (x) H_inn + H_out, H_inn = H_1 (0-based: H_0).
+ *   Sec. 2, eq. "P_s": orthonormal change of basis, P_s^{-1} = P_s.
+ *   Sec. 2, eqs. "hL_s", "hL_splitting": P_s A P_s = blockdiag(A^_i),
+ *       A^_i = A_inn + A_out,i.
+ *   Alg. 1 ("symsolver"): b^ = P_s b; solve A^_i x^_i = b^_i for all i; x = P_s x^.
+ *   Sec. 2.2, eqs. "AMGinn", "LRCAMG" (k = 0): the preconditioner I (x) M_inn^{-1},
+ *       one AMG hierarchy of A_inn applied to all 2^s blocks by SpMM.
+ *   Sec. 5: PCG outer iteration; AMG = PMIS coarsening, extended+i
+ *       interpolation, FSAI smoother, direct coarsest solve.
+ *
+ * Conventions (every entry point):
+ *   - Indices are 0-based.  Copy j of the base mesh is the base reflected
+ *     across every axis whose bit is set in j (copy 0 = the base itself).
+ *   - "host" pointers are ordinary CPU memory; the library copies what it
+ *     keeps, the caller keeps ownership.  "device" pointers are CUDA global
+ *     memory of the current device, owned by the caller, and are used
+ *     asynchronously on the caller's stream (`stream`, a cudaStream_t; NULL =
+ *     legacy default stream).
+ *   - Natural-order device vectors are FP64, `nrhs` vectors of length n with
+ *     leading dimension `ld` >= n (vector r starts at ptr + r*ld).
+ *   - Reduced (transformed) device arrays are interleaved: shape [n_b][c]
+ *     row-major with c = nrhs * 2^s columns, column rhs*2^s + i holding block
+ *     i of right-hand side rhs.  They carry the unnormalised Walsh-Hadamard
+ *     transform, i.e. 2^{s/2} * P_s b (see amgsym_transform_forward).
+ *   - No exception crosses the ABI.  A negative status is an error; the
+ *     message is available from amgsym_last_error() (thread-local).  A
+ *     positive status is a warning with valid outputs.
+ *   - Not thread-safe per handle: one thread may use a handle at a time.
+ */
+#ifndef AMGSYM_H
+#define AMGSYM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amgsym_problem* amgsym_t;
+
+typedef enum {
+  AMGSYM_OK = 0,
+  AMGSYM_NOT_CONVERGED = 1,        /* warning: maxit reached, outputs valid */
+  AMGSYM_ERR_ARG = -1,             /* bad argument (null pointer, size, range) */
+  AMGSYM_ERR_MAP = -2,             /* symmetry map is not a bijection / bad shape */
+  AMGSYM_ERR_NOT_SYMMETRIC = -3,   /* matrix violates the block structure of
+                                      eq. "struct_2sym" or is not symmetric */
+  AMGSYM_ERR_NOT_SPD = -4,         /* non-positive diagonal or pivot in setup */
+  AMGSYM_ERR_BREAKDOWN = -5,       /* PCG breakdown (p^T A p <= 0 or NaN) */
+  AMGSYM_ERR_CUDA = -6,            /* CUDA runtime error */
+  AMGSYM_ERR_OOM = -7,             /* host or device allocation failed */
+  AMGSYM_ERR_DEVICE_TIMEOUT = -8,  /* a bounded device-side wait gave up */
+  AMGSYM_ERR_STATE = -9            /* call out of order (e.g. solve before setup) */
+} amgsym_status;
+
+/* Arithmetic of a solve. */
+enum {
+  AMGSYM_PREC_FP64 = 0,       /* FP64 vectors, matrices, V-cycle and PCG */
+  AMGSYM_PREC_MIXED_FP32 = 1, /* FP64 iterative refinement around an inner PCG
+                                 with FP32 vectors and FP32 matrix values; FP64
+                                 CG scalars, dot-product accumulation and
+                                 coarsest solve */
+  AMGSYM_PREC_MIXED_BF16 = 2  /* as MIXED_FP32, but the V-cycle's matrices
+                                 (A_l for l >= 0, G, G^T, P, R) stored as BF16
+                                 values, computed in FP32 */
+};
+
+/* AMG setup parameters (Sec. 5; the paper does not fix theta, omega, the
+ * coarse size or the FSAI pattern for this path -- these are defaults). */
+typedef struct {
+  double strength_theta;    /* classical strength threshold, default 0.25 */
+  double interp_trunc;      /* drop interpolation weights < trunc * row max, 0.2 */
+  int32_t interp_max_elems; /* keep at most this many weights per row, 4 */
+  int32_t max_levels;       /* hierarchy depth limit, 25 */
+  int32_t coarse_max;       /* dense direct solve at or below this size, 256 */
+  int32_t fsai_max_lower;   /* FSAI pattern: strongest lower entries per row,
+                               diagonal included, default 8 */
+  double omega_scale;       /* smoother damping omega = omega_scale / lambda_max(G A G^T), 1.2 */
+  int32_t nu;               /* V(nu, nu) cycle, default 1 */
+  int32_t precisions;       /* bit mask of device copies to build:
+                               1 = FP64, 2 = FP32, 4 = BF16 (default 3) */
+  int32_t host_only;        /* 1: build the hierarchy on the host only, no
+                               device upload (hierarchy export / CPU tests) */
+  uint64_t seed;            /* PMIS random tie-breaking, default 12345 */
+} amgsym_opts;
+
+typedef struct {
+  double tol;          /* stop when ||b - A x||_2 / ||b||_2 <= tol per RHS, 1e-8 */
+  int32_t maxit;       /* max PCG iterations (FP64) / total inner iterations (mixed), 500 */
+  int32_t precision;   /* AMGSYM_PREC_*, default AMGSYM_PREC_FP64 */
+  int32_t use_x0;      /* 1: x_dev holds the initial guess; 0: start from zero */
+  double inner_tol;    /* mixed: inner PCG relative reduction per refinement step, 1e-4 */
+  int32_t max_outer;   /* mixed: refinement steps, 20 */
+  int32_t finest_hat;  /* 1: V-cycle finest-level residuals use A^_i instead of A_inn */
+  int32_t use_graph;   /* 1: capture one PCG iteration in a CUDA graph and replay it */
+} amgsym_solve_opts;
+
+typedef struct {
+  int32_t iters;       /* PCG iterations (FP64) or total inner iterations (mixed) */
+  int32_t outer_iters; /* refinement steps (mixed), 0 for FP64 */
+  int32_t converged;   /* 1 if every RHS reached tol */
+  double* relres;      /* optional, caller-owned host array [nrhs]: final true
+                          relative residual of every RHS */
+} amgsym_solve_info;
+
+void amgsym_opts_default(amgsym_opts* o);
+void amgsym_solve_opts_default(amgsym_solve_opts* o);
+
+/* Thread-local message of the last error raised in this thread. */
+const char* amgsym_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Problem creation (host only, no CUDA call).
+ *
+ * amgsym_create_problem: the full n x n operator in CSR (host; rowptr
+ * [n+1] int64, colidx [nnz] int32, vals [nnz] FP64, any column order) and the
+ * symmetry map perm (host int32, [2^s][n/2^s] row-major): perm[j*n_b + l] =
+ * natural index of local cell l of copy j (Sec. 2, eq. "fields_struct").
+ * Validates that perm is a bijection (else AMGSYM_ERR_MAP) and that every
+ * entry satisfies A[perm(p,l), perm(q,l')] == H_{p XOR q}[l, l'] exactly with
+ * symmetric H_m (eq. "struct_2sym"; else AMGSYM_ERR_NOT_SYMMETRIC), then keeps
+ * A_inn = H_0 and the interface couplings H_m, m >= 1 (eq. "split_s"), i.e.
+ * memory / 2^s.  s = 0 is allowed (no symmetry, nb = 1).
+ * On success *out owns the problem; release it with amgsym_destroy.
+ * ---------------------------------------------------------------------- */
+amgsym_status amgsym_create_problem(int64_t n, const int64_t* rowptr, const int32_t* colidx,
+                                    const double* vals, int32_t s, const int32_t* perm,
+                                    amgsym_t* out);
+
+/* Sizes of a created problem (any pointer may be NULL). */
+amgsym_status amgsym_problem_sizes(amgsym_t h, int64_t* n, int64_t* n_b, int32_t* s,
+                                   int64_t* nnz_inn, int64_t* n_iface_rows,
+                                   int64_t* n_iface_entries);
+
+/* Host copies of A_inn (CSR, columns sorted: rowptr [n_b+1], colidx, vals [nnz_inn])
+ * and of the interface couplings: for each interface entry e (sorted by row
+ * then column), row[e], col[e] and the 2^s values
+ * vals[e*2^s + i] = (A_out,i)[row, col] = sum_{m>=1} (-1)^{popcount(i&m)} H_m[row, col]
+ * (eq. "hL_splitting").  Buffers are caller-owned and sized from
+ * amgsym_problem_sizes. */
+amgsym_status amgsym_get_inner_block(amgsym_t h, int64_t* rowptr, int32_t* colidx, double* vals);
+amgsym_status amgsym_get_interface(amgsym_t h, int32_t* row, int32_t* col, double* vals);
+
+/* ------------------------------------------------------------------------
+ * Setup: AMG hierarchy of A_inn on the host (PMIS, extended+i interpolation
+ * truncated, Galerkin R A P with R = P^T, static FSAI on the strongest lower
+ * pattern, dense inverse at the coarsest level; Sec. 5), then upload of the
+ * problem and hierarchy to the current CUDA device (unless opts->host_only).
+ * opts may be NULL (defaults).  May be called again to rebuild.
+ * ---------------------------------------------------------------------- */
+amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts);
+
+/* Hierarchy export (host copies, for inspection and tests).
+ * amgsym_num_levels: number of levels L (level L-1 is the dense coarsest).
+ * amgsym_level_sizes: rows and nnz of A_l, P_l (n_l x n_{l+1}) and G_l;
+ *   P_l and G_l are absent (0) on the coarsest level.
+ * amgsym_get_level_matrix: which = 0 A_l, 1 P_l, 2 G_l; CSR into caller buffers
+ *   (rowptr [rows+1], colidx, vals [nnz]).  *omega receives the smoother damping. */
+int32_t amgsym_num_levels(amgsym_t h);
+amgsym_status amgsym_level_sizes(amgsym_t h, int32_t level, int64_t* rows, int64_t* nnz_A,
+                                 int64_t* nnz_P, int64_t* cols_P, int64_t* nnz_G, double* omega);
+amgsym_status amgsym_get_level_matrix(amgsym_t h, int32_t level, int32_t which,
+                                      int64_t* rowptr, int32_t* colidx, double* vals);
+
+/* ------------------------------------------------------------------------
+ * Solve (Alg. 1): x = A^{-1} b for nrhs right-hand sides.
+ * b_dev, x_dev: device FP64 natural order, [nrhs][ld].  x_dev is the initial
+ * guess if sopts->use_x0, else ignored on input.  sopts may be NULL
+ * (defaults).  info may be NULL; when given, the call synchronises the stream
+ * and fills it.  Returns AMGSYM_NOT_CONVERGED if maxit was reached.
+ * Work arrays are allocated on the device on first use for a given nrhs
+ * (grow-only) and freed by amgsym_destroy.
+ * ---------------------------------------------------------------------- */
+amgsym_status amgsym_solve(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs,
+                           int64_t ld, const amgsym_solve_opts* sopts, void* stream,
+                           amgsym_solve_info* info);
+
+/* Adjoint solve A^T lambda = g.  A is symmetric, so this is the same reduced
+ * solve; kept as its own entry point for the differentiable interface. */
+amgsym_status amgsym_solve_adjoint(amgsym_t h, const double* g_dev, double* lam_dev,
+                                   int32_t nrhs, int64_t ld, const amgsym_solve_opts* sopts,
+                                   void* stream, amgsym_solve_info* info);
+
+/* ------------------------------------------------------------------------
+ * Individual steps of the solve (device; after amgsym_setup), for testing and
+ * composition.  `prec` selects FP64 (AMGSYM_PREC_FP64: double arrays) or FP32
+ * (any mixed mode: float arrays) for the reduced arrays.
+ * ---------------------------------------------------------------------- */
+
+/* Forward transform (Alg. 1, first step; eq. "P_s"):
+ * xhat[l][r*2^s + i] = sum_j (-1)^{popcount(i&j)} b_r[perm(j, l)]  (= 2^{s/2} P_s b),
+ * b_dev FP64 natural [nrhs][ld], xhat_dev FP64 [n_b][nrhs*2^s]. */
+amgsym_status amgsym_transform_forward(amgsym_t h, const double* b_dev, int32_t nrhs, int64_t ld,
+                                       double* xhat_dev, void* stream);
+
+/* Backward transform (Alg. 1, last step; P_s^{-1} = P_s):
+ * x_r[perm(j, l)] = 2^{-s} sum_i (-1)^{popcount(i&j)} xhat[l][r*2^s + i].
+ * Applied to the output of amgsym_transform_forward it returns b exactly
+ * up to rounding (the 2^{-s} scale undoes both unnormalised transforms). */
+amgsym_status amgsym_transform_backward(amgsym_t h, const double* xhat_dev, int32_t nrhs,
+                                        double* x_dev, int64_t ld, void* stream);
+
+/* Reduced operator (eq. "hL_splitting"):
+ * Y[:, c] = A_inn X[:, c] + A_out,(c mod 2^s) X[:, c] for all columns at once,
+ * A_inn read once for all columns.  X, Y: [n_b][nrhs*2^s], double (prec FP64)
+ * or float (mixed).  X and Y must not overlap. */
+amgsym_status amgsym_apply_reduced(amgsym_t h, const void* X_dev, void* Y_dev, int32_t nrhs,
+                                   int32_t prec, void* stream);
+
+/* Preconditioner (eqs. "AMGinn", "LRCAMG" with k = 0): Z = (I (x) M_inn^{-1}) R,
+ * one symmetric V(nu, nu) cycle of the A_inn hierarchy applied to every
+ * column; with finest_hat = 1 the finest-level residuals use A^_i.
+ * R, Z: [n_b][nrhs*2^s], double (FP64) or float (mixed); must not overlap. */
+amgsym_status amgsym_vcycle(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs,
+                            int32_t prec, int32_t finest_hat, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Structured-grid problem generator (host): the unit cube with N[a] cells
+ * per axis (d = 1..3), cell-centred finite volumes for -div(k grad u) = f,
+ * homogeneous Dirichlet.  Face transmissibility t_f = area_f /
+ * sum_{c in f} h_c / (2 k_c) (a boundary face has the single cell term);
+ * A_pq = -t_f, A_pp = sum over faces (per-axis low+high pairs summed first).
+ * Natural order, x fastest.  Stretching: eq. "tanh" (Sec. 2.2).
+ * ---------------------------------------------------------------------- */
+
+/* Cell widths of an N-cell axis: uniform (gamma = 0) or eq. "tanh" with
+ * stretching gamma; for even N the upper half mirrors the lower half exactly. */
+amgsym_status amgsym_grid_widths(int64_t N, double gamma, double* widths_out);
+
+/* Number of stored entries of the 2d+1-point operator. */
+int64_t amgsym_fv_nnz(int32_t d, const int64_t* N);
+
+/* Assemble the full operator: widths = concatenation of the d per-axis width
+ * arrays (host), k = per-cell coefficient (host, natural order).  Outputs are
+ * caller-owned host buffers: rowptr [n+1], colidx/vals [amgsym_fv_nnz]. */
+amgsym_status amgsym_fv_assemble(int32_t d, const int64_t* N, const double* widths,
+                                 const double* k, int64_t* rowptr, int32_t* colidx,
+                                 double* vals);
+
+/* Mirrored-ordering map for s reflection symmetries of axes 0..s-1
+ * (perm as in amgsym_create_problem, host int32 [2^s][n/2^s]). */
+amgsym_status amgsym_mirror_perm(int32_t d, const int64_t* N, int32_t s, int32_t* perm);
+
+/* Adjoint gradient with respect to g = log k (device, FP64, natural order):
+ * grad[c] += sum over faces f of c of (dL/dt_f) * t_f^2 h_c / (2 area_f k_c),
+ * with dL/dt_f = -(lam_p - lam_q)(u_p - u_q) (interior) or -lam_p u_p
+ * (boundary), summed over nrhs pairs (u_r, lam_r) with leading dimension ld.
+ * widths_dev: concatenated per-axis widths (device); k_dev per cell.
+ * accumulate = 0 overwrites grad_dev, 1 adds to it. */
+amgsym_status amgsym_fv_grad_logk(int32_t d, const int64_t* N, const double* widths_dev,
+                                  const double* k_dev, const double* u_dev,
+                                  const double* lam_dev, int32_t nrhs, int64_t ld,
+                                  double* grad_dev, int32_t accumulate, void* stream);
+
+void amgsym_destroy(amgsym_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMGSYM_H */

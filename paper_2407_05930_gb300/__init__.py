@@ -1,0 +1,394 @@
+"""Python binding of the amgsym C ABI (``include/amgsym.h``).
+
+Symmetry-reduced AMG-preconditioned CG for the discrete Poisson equation
+(arXiv 2407.05930, Alg. 1 with the preconditioner ``I (x) M_inn^{-1}``).
+This module only marshals arguments: every step of the solve runs in the
+CUDA kernels of ``libamgsym.so``.  PyTorch supplies device memory and the
+current stream.  There is no CPU fallback: importing fails if the library
+has not been built (``paper_2407_05930_gb300.build.build()``), and the device
+entry points fail if no CUDA device is present.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libamgsym.so")
+
+PREC_FP64 = 0
+PREC_MIXED_FP32 = 1
+PREC_MIXED_BF16 = 2
+
+STATUS = {
+    0: "OK",
+    1: "NOT_CONVERGED",
+    -1: "ERR_ARG",
+    -2: "ERR_MAP",
+    -3: "ERR_NOT_SYMMETRIC",
+    -4: "ERR_NOT_SPD",
+    -5: "ERR_BREAKDOWN",
+    -6: "ERR_CUDA",
+    -7: "ERR_OOM",
+    -8: "ERR_DEVICE_TIMEOUT",
+    -9: "ERR_STATE",
+}
+
+
+class AmgsymError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("strength_theta", ctypes.c_double),
+        ("interp_trunc", ctypes.c_double),
+        ("interp_max_elems", ctypes.c_int32),
+        ("max_levels", ctypes.c_int32),
+        ("coarse_max", ctypes.c_int32),
+        ("fsai_max_lower", ctypes.c_int32),
+        ("omega_scale", ctypes.c_double),
+        ("nu", ctypes.c_int32),
+        ("precisions", ctypes.c_int32),
+        ("host_only", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("maxit", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("use_x0", ctypes.c_int32),
+        ("inner_tol", ctypes.c_double),
+        ("max_outer", ctypes.c_int32),
+        ("finest_hat", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int32),
+        ("outer_iters", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("relres", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with paper_2407_05930_gb300.build.build() "
+            "(there is no CPU fallback)"
+        )
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    pi64 = ctypes.POINTER(i64)
+    pi32 = ctypes.POINTER(i32)
+    pdbl = ctypes.POINTER(dbl)
+    sig = {
+        "amgsym_opts_default": (None, [ctypes.POINTER(Opts)]),
+        "amgsym_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
+        "amgsym_last_error": (ctypes.c_char_p, []),
+        "amgsym_create_problem": (i32, [i64, pi64, pi32, pdbl, i32, pi32, ctypes.POINTER(P)]),
+        "amgsym_problem_sizes": (i32, [P, pi64, pi64, pi32, pi64, pi64, pi64]),
+        "amgsym_get_inner_block": (i32, [P, pi64, pi32, pdbl]),
+        "amgsym_get_interface": (i32, [P, pi32, pi32, pdbl]),
+        "amgsym_setup": (i32, [P, ctypes.POINTER(Opts)]),
+        "amgsym_num_levels": (i32, [P]),
+        "amgsym_level_sizes": (i32, [P, i32, pi64, pi64, pi64, pi64, pi64, pdbl]),
+        "amgsym_get_level_matrix": (i32, [P, i32, i32, pi64, pi32, pdbl]),
+        "amgsym_solve": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
+        "amgsym_solve_adjoint": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
+        "amgsym_transform_forward": (i32, [P, P, i32, i64, P, P]),
+        "amgsym_transform_backward": (i32, [P, P, i32, P, i64, P]),
+        "amgsym_apply_reduced": (i32, [P, P, P, i32, i32, P]),
+        "amgsym_vcycle": (i32, [P, P, P, i32, i32, i32, P]),
+        "amgsym_grid_widths": (i32, [i64, dbl, pdbl]),
+        "amgsym_fv_nnz": (i64, [i32, pi64]),
+        "amgsym_fv_assemble": (i32, [i32, pi64, pdbl, pdbl, pi64, pi32, pdbl]),
+        "amgsym_mirror_perm": (i32, [i32, pi64, i32, pi32]),
+        "amgsym_fv_grad_logk": (i32, [i32, pi64, P, P, P, P, i32, i64, P, i32, P]),
+        "amgsym_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+#: C-ABI entry points declared in include/amgsym.h
+EXPORTED = [
+    name
+    for name in (
+        "amgsym_opts_default amgsym_solve_opts_default amgsym_last_error amgsym_create_problem "
+        "amgsym_problem_sizes amgsym_get_inner_block amgsym_get_interface amgsym_setup "
+        "amgsym_num_levels amgsym_level_sizes amgsym_get_level_matrix amgsym_solve "
+        "amgsym_solve_adjoint amgsym_transform_forward amgsym_transform_backward "
+        "amgsym_apply_reduced amgsym_vcycle amgsym_grid_widths amgsym_fv_nnz "
+        "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_destroy"
+    ).split()
+]
+
+
+def _check(code: int):
+    if code < 0:
+        raise AmgsymError(code, lib.amgsym_last_error().decode())
+    return code
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib.amgsym_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown setup option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def default_solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib.amgsym_solve_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown solve option {k}")
+        setattr(o, k, v)
+    return o
+
+
+# ----------------------------------------------------------------------------
+# structured-grid generator (host)
+
+def grid_widths(N: int, gamma: float) -> np.ndarray:
+    w = np.empty(int(N), dtype=np.float64)
+    _check(lib.amgsym_grid_widths(int(N), float(gamma), _ptr(w, ctypes.c_double)))
+    return w
+
+
+def fv_assemble(N, widths, k):
+    """Full operator of the structured grid: (rowptr int64, colidx int32, vals f64)."""
+    N = np.ascontiguousarray(N, dtype=np.int64)
+    d = N.size
+    nnz = lib.amgsym_fv_nnz(d, _ptr(N, ctypes.c_int64))
+    n = int(np.prod(N))
+    W = np.ascontiguousarray(np.concatenate([np.asarray(w, dtype=np.float64) for w in widths]))
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    if k.size != n:
+        raise ValueError("k must have one value per cell")
+    rowptr = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    _check(lib.amgsym_fv_assemble(d, _ptr(N, ctypes.c_int64), _ptr(W, ctypes.c_double), _ptr(k, ctypes.c_double),
+                                  _ptr(rowptr, ctypes.c_int64), _ptr(col, ctypes.c_int32), _ptr(val, ctypes.c_double)))
+    return rowptr, col, val
+
+
+def mirror_perm(N, s: int) -> np.ndarray:
+    N = np.ascontiguousarray(N, dtype=np.int64)
+    n = int(np.prod(N))
+    perm = np.empty(n, dtype=np.int32)
+    _check(lib.amgsym_mirror_perm(N.size, _ptr(N, ctypes.c_int64), int(s), _ptr(perm, ctypes.c_int32)))
+    return perm.reshape(1 << s, n >> s)
+
+
+@dataclass
+class SolveResult:
+    iters: int
+    outer_iters: int
+    converged: bool
+    relres: np.ndarray
+    status: str
+
+
+class Problem:
+    """A created problem (``amgsym_create_problem``) and, after ``setup``,
+    its AMG hierarchy on the device."""
+
+    def __init__(self, n, rowptr, colidx, vals, s, perm):
+        self._h = ctypes.c_void_p()
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        perm = np.ascontiguousarray(perm, dtype=np.int32)
+        _check(lib.amgsym_create_problem(int(n), _ptr(rowptr, ctypes.c_int64), _ptr(colidx, ctypes.c_int32),
+                                         _ptr(vals, ctypes.c_double), int(s), _ptr(perm, ctypes.c_int32),
+                                         ctypes.byref(self._h)))
+        self.n = int(n)
+        self.s = int(s)
+        self.nb = 1 << self.s
+        self.n_b = self.n >> self.s
+        self.grid = None
+
+    @classmethod
+    def structured(cls, N, gamma: float = 0.0, logk: Optional[np.ndarray] = None, s: int = 0):
+        """Unit-cube finite-volume problem with N cells per axis and s mirror symmetries."""
+        N = tuple(int(v) for v in N)
+        widths = [grid_widths(n, gamma) for n in N]
+        n = int(np.prod(N))
+        k = np.ones(n) if logk is None else np.exp(np.asarray(logk, dtype=np.float64))
+        rowptr, col, val = fv_assemble(N, widths, k)
+        perm = mirror_perm(N, s)
+        p = cls(n, rowptr, col, val, s, perm)
+        p.grid = dict(N=N, widths=widths, k=k)
+        return p
+
+    def close(self):
+        if self._h:
+            lib.amgsym_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- host
+    def sizes(self):
+        n, n_b, nnz, nir, nie = (ctypes.c_int64() for _ in range(5))
+        s = ctypes.c_int32()
+        _check(lib.amgsym_problem_sizes(self._h, ctypes.byref(n), ctypes.byref(n_b), ctypes.byref(s),
+                                        ctypes.byref(nnz), ctypes.byref(nir), ctypes.byref(nie)))
+        return dict(n=n.value, n_b=n_b.value, s=s.value, nnz_inn=nnz.value, n_iface_rows=nir.value,
+                    n_iface_entries=nie.value)
+
+    def inner_block(self):
+        sz = self.sizes()
+        rp = np.empty(sz["n_b"] + 1, dtype=np.int64)
+        ci = np.empty(sz["nnz_inn"], dtype=np.int32)
+        v = np.empty(sz["nnz_inn"], dtype=np.float64)
+        _check(lib.amgsym_get_inner_block(self._h, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32),
+                                          _ptr(v, ctypes.c_double)))
+        return rp, ci, v
+
+    def interface(self):
+        sz = self.sizes()
+        ne = sz["n_iface_entries"]
+        r = np.empty(max(ne, 1), dtype=np.int32)
+        c = np.empty(max(ne, 1), dtype=np.int32)
+        v = np.empty(max(ne, 1) * self.nb, dtype=np.float64)
+        _check(lib.amgsym_get_interface(self._h, _ptr(r, ctypes.c_int32), _ptr(c, ctypes.c_int32),
+                                        _ptr(v, ctypes.c_double)))
+        return r[:ne], c[:ne], v[: ne * self.nb].reshape(ne, self.nb)
+
+    def setup(self, **kw):
+        o = default_opts(**kw)
+        _check(lib.amgsym_setup(self._h, ctypes.byref(o)))
+        return self
+
+    def num_levels(self) -> int:
+        return int(lib.amgsym_num_levels(self._h))
+
+    def level_info(self, level: int):
+        rows, nA, nP, cP, nG = (ctypes.c_int64() for _ in range(5))
+        om = ctypes.c_double()
+        _check(lib.amgsym_level_sizes(self._h, level, ctypes.byref(rows), ctypes.byref(nA), ctypes.byref(nP),
+                                      ctypes.byref(cP), ctypes.byref(nG), ctypes.byref(om)))
+        return dict(rows=rows.value, nnz_A=nA.value, nnz_P=nP.value, cols_P=cP.value, nnz_G=nG.value,
+                    omega=om.value)
+
+    def level_matrix(self, level: int, which: str):
+        """Host CSR (rowptr, colidx, vals, shape) of A, P or G on a level."""
+        info = self.level_info(level)
+        w = {"A": 0, "P": 1, "G": 2}[which]
+        rows = info["rows"]
+        nnz = {"A": info["nnz_A"], "P": info["nnz_P"], "G": info["nnz_G"]}[which]
+        cols = info["cols_P"] if which == "P" else rows
+        rp = np.empty(rows + 1, dtype=np.int64)
+        ci = np.empty(max(nnz, 1), dtype=np.int32)
+        v = np.empty(max(nnz, 1), dtype=np.float64)
+        _check(lib.amgsym_get_level_matrix(self._h, level, w, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32),
+                                           _ptr(v, ctypes.c_double)))
+        return rp, ci[:nnz], v[:nnz], (rows, cols)
+
+    # ---------------------------------------------------------------- device
+    @staticmethod
+    def _stream():
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def solve(self, b, x=None, adjoint: bool = False, **kw) -> SolveResult:
+        """Solve A x = b.  b: CUDA float64 tensor [n] or [nrhs, n] (natural order).
+        x: optional output tensor of the same shape (initial guess with use_x0=1)."""
+        import torch
+
+        if not (isinstance(b, torch.Tensor) and b.is_cuda and b.dtype == torch.float64):
+            raise TypeError("b must be a CUDA float64 tensor")
+        bb = b.reshape(-1, self.n)
+        if not bb.is_contiguous():
+            bb = bb.contiguous()
+        nrhs = bb.shape[0]
+        if x is None:
+            x = torch.empty_like(bb)
+        xx = x.reshape(-1, self.n)
+        o = default_solve_opts(**kw)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        info = SolveInfo()
+        info.relres = _ptr(rel, ctypes.c_double)
+        fn = lib.amgsym_solve_adjoint if adjoint else lib.amgsym_solve
+        code = fn(self._h, ctypes.c_void_p(bb.data_ptr()), ctypes.c_void_p(xx.data_ptr()), nrhs, self.n,
+                  ctypes.byref(o), self._stream(), ctypes.byref(info))
+        _check(code)
+        res = SolveResult(info.iters, info.outer_iters, bool(info.converged), rel, STATUS[code])
+        return x if x.shape == b.shape else xx.reshape(b.shape), res
+
+    def solve_async(self, b, x, nrhs: int, **kw) -> int:
+        """Launch a solve without reading back its info (no host synchronisation
+        beyond the convergence checks); returns the status code."""
+        o = default_solve_opts(**kw)
+        return _check(lib.amgsym_solve(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs,
+                                       self.n, ctypes.byref(o), self._stream(), None))
+
+    def transform_forward(self, b, nrhs: int, out):
+        _check(lib.amgsym_transform_forward(self._h, ctypes.c_void_p(b.data_ptr()), nrhs, self.n,
+                                            ctypes.c_void_p(out.data_ptr()), self._stream()))
+        return out
+
+    def transform_backward(self, xhat, nrhs: int, out):
+        _check(lib.amgsym_transform_backward(self._h, ctypes.c_void_p(xhat.data_ptr()), nrhs,
+                                             ctypes.c_void_p(out.data_ptr()), self.n, self._stream()))
+        return out
+
+    def apply_reduced(self, X, Y, nrhs: int, prec: int = PREC_FP64):
+        _check(lib.amgsym_apply_reduced(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                        nrhs, prec, self._stream()))
+        return Y
+
+    def vcycle(self, R, Z, nrhs: int, prec: int = PREC_FP64, finest_hat: bool = False):
+        _check(lib.amgsym_vcycle(self._h, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()), nrhs, prec,
+                                 1 if finest_hat else 0, self._stream()))
+        return Z
+
+
+def fv_grad_logk(N, widths_dev, k_dev, u_dev, lam_dev, grad_dev, nrhs: int = 1, accumulate: bool = False):
+    """Adjoint coefficient gradient on the device (see include/amgsym.h)."""
+    import torch
+
+    N = np.ascontiguousarray(N, dtype=np.int64)
+    n = int(np.prod(N))
+    _check(lib.amgsym_fv_grad_logk(N.size, _ptr(N, ctypes.c_int64), ctypes.c_void_p(widths_dev.data_ptr()),
+                                   ctypes.c_void_p(k_dev.data_ptr()), ctypes.c_void_p(u_dev.data_ptr()),
+                                   ctypes.c_void_p(lam_dev.data_ptr()), nrhs, n, ctypes.c_void_p(grad_dev.data_ptr()),
+                                   1 if accumulate else 0,
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return grad_dev

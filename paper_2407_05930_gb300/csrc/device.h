@@ -1,0 +1,149 @@
+// Device-side types and kernel launchers shared by the .cu translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+namespace amgsym {
+
+// Matrix value storage of a device matrix.
+enum ValType { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
+// Vector storage.
+enum VecType { VEC_F64 = 0, VEC_F32 = 1 };
+
+// CSR on the device with 32-bit row pointers and columns; one value array
+// per precision that was built.
+struct DevCsr {
+  int32_t rows = 0, cols = 0;
+  int64_t nnz = 0;
+  int32_t* ptr = nullptr;
+  int32_t* idx = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  __nv_bfloat16* v16 = nullptr;
+  const void* vals(ValType t) const {
+    return t == VAL_F64 ? (const void*)v64 : t == VAL_F32 ? (const void*)v32 : (const void*)v16;
+  }
+};
+
+// Interface couplings A_out,i of eq. "hL_splitting" in a form the SpMM can
+// look up per row at ~0.25 byte per row: a bit per row (is there any
+// coupling?) and, per 32-row word, the number of flagged rows before it.
+struct DevIface {
+  int32_t n_rows_flagged = 0;
+  int64_t n_entries = 0;
+  uint32_t* mask = nullptr;    // ceil(n_b / 32)
+  int32_t* prefix = nullptr;   // ceil(n_b / 32)
+  int32_t* iptr = nullptr;     // n_rows_flagged + 1
+  int32_t* icol = nullptr;     // n_entries
+  double* ival64 = nullptr;    // n_entries * nb
+  float* ival32 = nullptr;     // n_entries * nb
+};
+
+struct DevLevel {
+  int32_t n = 0;
+  DevCsr A, P, R, G, Gt;
+  double omega = 1.0;
+  double* cinv = nullptr;  // coarsest: dense inverse, FP64 row-major n x n
+};
+
+// Per-column CG scalars and solve status (device).
+struct DevScalars {
+  double* rz = nullptr;      // <r, z> per column
+  double* alpha = nullptr;
+  double* beta = nullptr;
+  double* rr = nullptr;      // <r, r> per column (last computed)
+  double* bnorm2 = nullptr;  // ||b^||^2 per RHS (reference for the stopping test)
+  double* relres = nullptr;  // per RHS
+  int32_t* active = nullptr; // per column: 1 while its RHS has not converged
+  int32_t* status = nullptr; // [0] active RHS count, [1] breakdown flag, [2] iterations
+  double* partials = nullptr;  // dot-product block partials
+  unsigned* ticket = nullptr;  // last-block counter
+  int64_t partial_cap = 0;     // doubles available in partials
+};
+
+// Tolerance block for the convergence finalisation.
+struct ConvParams {
+  double tol2;       // tol^2
+  int32_t nrhs, nb;  // columns = nrhs * nb
+  int32_t count_iter;
+};
+
+// Dot-product finalisation modes (executed by the last block of a kernel).
+enum DotFinal {
+  FIN_NONE = 0,
+  FIN_STORE_RZ = 1,  // rz[c] = sum
+  FIN_ALPHA = 2,     // alpha[c] = active ? rz[c] / sum : 0 ; breakdown check
+  FIN_BETA = 3,      // beta[c] = active ? sum / rz[c] : 0 ; rz[c] = sum
+  FIN_CONV = 4,      // rr[c] = sum ; per-RHS relres = sqrt(sum rr)/||b|| ; deactivate converged
+  FIN_STORE_BN = 5   // bnorm2[rhs] = sum over the RHS's columns
+};
+
+enum DotMode { DOT_NONE = 0, DOT_WY = 1, DOT_YY = 2 };
+
+struct DotArgs {
+  int32_t mode = DOT_NONE;
+  int32_t final = FIN_NONE;
+  const void* W = nullptr;  // partner vector for DOT_WY (XT layout [rows][C])
+  DevScalars sc;
+  ConvParams cp{};
+};
+
+struct SpmmArgs {
+  int32_t rows = 0, C = 0;
+  const int32_t* ptr = nullptr;
+  const int32_t* idx = nullptr;
+  const void* val = nullptr;
+  const void* X = nullptr;
+  void* Y = nullptr;
+  const void* Z = nullptr;  // epilogue operand (XT)
+  double alpha = 1.0, beta = 0.0;
+  // Interface correction (NULL mask = none).
+  const uint32_t* imask = nullptr;
+  const int32_t* iprefix = nullptr;
+  const int32_t* iptr = nullptr;
+  const int32_t* icol = nullptr;
+  const void* ival = nullptr;  // same precision class as the accumulation
+  int32_t nb = 1;
+  DotArgs dot;
+};
+
+// Launchers (k_spmm.cu).  mt: matrix values, xt: X/Z/W vectors, ot: Y.
+void launch_spmm(ValType mt, VecType xt, VecType ot, const SpmmArgs& a, cudaStream_t st);
+
+// Elementwise / transform / small kernels (k_misc.cu).
+void launch_transform_fwd(const double* b, int32_t nrhs, int64_t ld, const int32_t* perm, int64_t n_b,
+                          int32_t s, void* xhat, VecType ot, cudaStream_t st);
+void launch_transform_bwd(const void* xhat, VecType it, int32_t nrhs, const int32_t* perm, int64_t n_b,
+                          int32_t s, double* x, int64_t ld, cudaStream_t st);
+// x += alpha p ; r -= alpha q ; rr = <r, r>  (finalisation FIN_CONV)
+void launch_cg_update1(VecType vt, int64_t rows, int32_t C, void* x, void* r, const void* p,
+                       const void* q, const DotArgs& dot, cudaStream_t st);
+// p = z + beta p
+void launch_cg_update2(VecType vt, int64_t rows, int32_t C, void* p, const void* z,
+                       const double* beta, cudaStream_t st);
+// y (f64) += x (f32 or f64)
+void launch_add_to_f64(VecType xt, int64_t count, double* y, const void* x, cudaStream_t st);
+void launch_copy(VecType vt, int64_t count, void* dst, const void* src, cudaStream_t st);
+void launch_zero(VecType vt, int64_t count, void* dst, cudaStream_t st);
+// dot over a whole [rows][C] array (for ||b^||^2 etc.)
+void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,
+                cudaStream_t st);
+// Z = Ainv Y (dense coarsest solve, FP64 arithmetic)
+void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
+                         cudaStream_t st);
+// CG initial scalars: active = 1 for columns of RHS with nonzero ||b||, status reset.
+void launch_init_scalars(const DevScalars& sc, int32_t nrhs, int32_t nb, cudaStream_t st);
+void launch_fv_grad(int32_t d, const int64_t* N, const double* widths, const double* k, const double* u,
+                    const double* lam, int32_t nrhs, int64_t ld, double* grad, int32_t accumulate,
+                    cudaStream_t st);
+
+int num_sms();
+int max_grid_blocks();  // blocks for grid-stride kernels (SMs x resident blocks)
+
+}  // namespace amgsym

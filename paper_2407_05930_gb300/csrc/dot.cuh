@@ -1,0 +1,127 @@
+// Deterministic per-column dot products fused into kernel epilogues.
+//
+// Every participating kernel uses 256-thread blocks in which thread t owns
+// the CPT consecutive columns c0 = (t % TPR) * CPT of row slot t / TPR.  A
+// block reduces its threads' partials in shared memory in a fixed order,
+// writes one partial per column to global memory, and the last block to
+// finish (integer ticket) sums the block partials in a fixed order and runs
+// the finalisation (CG scalars, convergence test).  No floating-point
+// atomics: results are bit-reproducible run to run.
+#pragma once
+
+#include "device.h"
+
+namespace amgsym {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ void dot_finalize_column(const DotArgs& d, int c, double sum) {
+  DevScalars s = d.sc;
+  switch (d.final) {
+    case FIN_STORE_RZ:
+      s.rz[c] = sum;
+      break;
+    case FIN_ALPHA: {
+      const double rz = s.rz[c];
+      double a = 0.0;
+      if (s.active[c] && rz != 0.0) {
+        if (sum > 0.0 && isfinite(sum)) a = rz / sum;
+        else s.status[1] = 1;  // breakdown: p^T A p <= 0 or NaN
+      }
+      s.alpha[c] = a;
+      break;
+    }
+    case FIN_BETA: {
+      const double rz = s.rz[c];
+      s.beta[c] = (s.active[c] && rz != 0.0) ? sum / rz : 0.0;
+      s.rz[c] = sum;
+      break;
+    }
+    case FIN_CONV:
+      s.rr[c] = sum;
+      break;
+    default:
+      break;
+  }
+}
+
+// Per-RHS stage of FIN_CONV / FIN_STORE_BN; colsum in shared memory [C].
+__device__ __forceinline__ void dot_finalize_rhs(const DotArgs& d, const double* colsum) {
+  DevScalars s = d.sc;
+  const int nrhs = d.cp.nrhs, nb = d.cp.nb;
+  if (d.final == FIN_STORE_BN) {
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+      double t = 0.0;
+      for (int i = 0; i < nb; ++i) t += colsum[r * nb + i];
+      s.bnorm2[r] = t;
+    }
+    return;
+  }
+  if (d.final != FIN_CONV) return;
+  __shared__ int n_active;
+  if (threadIdx.x == 0) n_active = 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+    double t = 0.0;
+    for (int i = 0; i < nb; ++i) t += colsum[r * nb + i];
+    const double bn = s.bnorm2[r];
+    const double rel2 = bn > 0.0 ? t / bn : 0.0;
+    s.relres[r] = sqrt(rel2);
+    bool act = s.active[r * nb] != 0;
+    if (act && !(rel2 > d.cp.tol2)) {  // converged (NaN keeps it active)
+      act = false;
+      for (int i = 0; i < nb; ++i) s.active[r * nb + i] = 0;
+    }
+    if (act) atomicAdd(&n_active, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s.status[0] = n_active;
+    if (d.cp.count_iter) s.status[2] += 1;
+  }
+}
+
+// Block + grid reduction.  part[q] is this thread's partial for column
+// c0 + q (ignored when !has_cols).  Shared scratch: kBlock * CPT + 2 * 256 doubles.
+template <int CPT>
+__device__ __forceinline__ void block_dot(const DotArgs& d, const double (&part)[CPT], int c0, bool has_cols,
+                                          int rloc, int rows_pb, int C, double* sm) {
+  if (has_cols) {
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) sm[rloc * C + c0 + q] = part[q];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double t = 0.0;
+    for (int r = 0; r < rows_pb; ++r) t += sm[r * C + c];
+    d.sc.partials[(int64_t)blockIdx.x * C + c] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  __shared__ unsigned is_last;
+  if (threadIdx.x == 0) is_last = (atomicAdd(d.sc.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int slices = blockDim.x / C;  // C <= 256 = blockDim
+  double* red = sm;                   // [slices][C]
+  if ((int)threadIdx.x < slices * C) {
+    const int c = threadIdx.x % C, sl = threadIdx.x / C;
+    double t = 0.0;
+    for (int b = sl; b < (int)gridDim.x; b += slices) t += __ldcg(d.sc.partials + (int64_t)b * C + c);
+    red[sl * C + c] = t;
+  }
+  __syncthreads();
+  double* colsum = sm + kBlock;  // [C]
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double t = 0.0;
+    for (int sl = 0; sl < slices; ++sl) t += red[sl * C + c];
+    colsum[c] = t;
+    dot_finalize_column(d, c, t);
+  }
+  __syncthreads();
+  dot_finalize_rhs(d, colsum);
+  if (threadIdx.x == 0) *d.sc.ticket = 0u;
+}
+
+}  // namespace amgsym

@@ -1,0 +1,77 @@
+// Internal host-side types of the amgsym library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/amgsym.h"
+
+namespace amgsym {
+
+// Host CSR matrix with int64 row pointers (columns need not be sorted unless
+// stated by the producer).
+struct Csr {
+  int64_t rows = 0, cols = 0;
+  std::vector<int64_t> ptr;   // rows + 1
+  std::vector<int32_t> idx;
+  std::vector<double> val;
+  int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+// Error raised inside the library; converted to a status at the ABI.
+struct Error {
+  amgsym_status code;
+  std::string msg;
+};
+[[noreturn]] void fail(amgsym_status code, const std::string& msg);
+void set_last_error(const std::string& msg);
+
+// One level of the AMG hierarchy of A_inn (host copies).
+struct HostLevel {
+  Csr A;        // level operator (level 0: A_inn)
+  Csr P;        // prolongation n_l x n_{l+1} (absent on the coarsest level)
+  Csr R;        // restriction P^T
+  Csr G;        // FSAI factor, lower triangular (G^T G ~ A^{-1})
+  Csr Gt;       // G^T
+  double omega = 1.0;
+  double lambda_max = 0.0;
+  std::vector<double> coarse_inv;  // coarsest level: dense A^{-1}, row-major
+};
+
+struct HostHierarchy {
+  std::vector<HostLevel> levels;
+};
+
+struct Device;  // device-resident copies and work arrays (solve.cu)
+
+}  // namespace amgsym
+
+struct amgsym_problem {
+  int64_t n = 0;      // full unknowns
+  int64_t n_b = 0;    // base-block rows, n / 2^s
+  int32_t s = 0;
+  int32_t nb = 1;     // 2^s
+  amgsym::Csr Ainn;   // H_0, columns sorted
+  // Interface couplings: entries sorted by (row, col); ivals[e * nb + i] =
+  // (A_out,i)[row, col].
+  std::vector<int32_t> irow, icol;
+  std::vector<double> ivals;
+  std::vector<int32_t> perm;  // [nb][n_b]
+  amgsym_opts opts{};
+  bool have_hierarchy = false;
+  amgsym::HostHierarchy H;
+  amgsym::Device* dev = nullptr;
+};
+
+namespace amgsym {
+// host_amg.cpp
+void build_hierarchy(const Csr& A, const amgsym_opts& o, HostHierarchy& H);
+Csr transpose(const Csr& A);
+Csr spgemm(const Csr& A, const Csr& B);
+void sort_rows(Csr& A);
+// solve.cu
+void device_upload(amgsym_problem* p);
+void device_free(amgsym_problem* p);
+}  // namespace amgsym

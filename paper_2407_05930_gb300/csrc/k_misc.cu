@@ -1,0 +1,425 @@
+// Symmetry transforms, PCG vector updates, the dense coarsest-level solve and
+// the adjoint coefficient gradient.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device.h"
+#include "dot.cuh"
+
+namespace amgsym {
+
+static int g_sms = 0;
+
+int num_sms() {
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+// Grid-stride kernels run 8 resident 256-thread blocks per SM (2048 threads).
+int max_grid_blocks() { return num_sms() * 8; }
+
+static int grid_for(int64_t work, int per_block) {
+  int64_t g = (work + per_block - 1) / per_block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, max_grid_blocks()));
+}
+
+// ---------------------------------------------------------------------------
+// Forward transform (Alg. 1, "Transform forward"; eq. "P_s" without the
+// 2^{-s/2} factor): gather the 2^s mirror images of every base cell through
+// perm, then s butterfly stages (a + b, a - b).  One thread per (rhs, l);
+// consecutive threads take consecutive l so the gathers of each copy and the
+// interleaved writes are coalesced.
+
+template <int S, typename OT>
+__global__ void __launch_bounds__(kBlock) transform_fwd_kernel(const double* __restrict__ b, int32_t nrhs,
+                                                               int64_t ld, const int32_t* __restrict__ perm,
+                                                               int64_t n_b, OT* __restrict__ xhat) {
+  constexpr int NB = 1 << S;
+  const int64_t total = n_b * nrhs;
+  const int64_t C = (int64_t)nrhs * NB;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n_b, l = t - r * n_b;
+    double v[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) v[j] = __ldcs(b + r * ld + __ldcs(perm + j * n_b + l));
+#pragma unroll
+    for (int st = 0; st < S; ++st) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (!(i & (1 << st))) {
+          const double a0 = v[i], a1 = v[i | (1 << st)];
+          v[i] = a0 + a1;
+          v[i | (1 << st)] = a0 - a1;
+        }
+    }
+    OT* o = xhat + l * C + r * NB;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) o[i] = (OT)v[i];
+  }
+}
+
+template <int S, typename IT>
+__global__ void __launch_bounds__(kBlock) transform_bwd_kernel(const IT* __restrict__ xhat, int32_t nrhs,
+                                                               const int32_t* __restrict__ perm, int64_t n_b,
+                                                               double* __restrict__ x, int64_t ld) {
+  constexpr int NB = 1 << S;
+  const int64_t total = n_b * nrhs;
+  const int64_t C = (int64_t)nrhs * NB;
+  const double scale = 1.0 / (double)NB;  // 2^{-s}: exact
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n_b, l = t - r * n_b;
+    double v[NB];
+    const IT* in = xhat + l * C + r * NB;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) v[i] = (double)in[i];
+#pragma unroll
+    for (int st = 0; st < S; ++st) {
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (!(i & (1 << st))) {
+          const double a0 = v[i], a1 = v[i | (1 << st)];
+          v[i] = a0 + a1;
+          v[i | (1 << st)] = a0 - a1;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) __stcs(x + r * ld + __ldcs(perm + j * n_b + l), v[j] * scale);
+  }
+}
+
+template <typename OT>
+static void fwd_dispatch(const double* b, int32_t nrhs, int64_t ld, const int32_t* perm, int64_t n_b, int32_t s,
+                         OT* xhat, cudaStream_t st) {
+  const int g = grid_for(n_b * nrhs, kBlock);
+  switch (s) {
+    case 0: transform_fwd_kernel<0, OT><<<g, kBlock, 0, st>>>(b, nrhs, ld, perm, n_b, xhat); break;
+    case 1: transform_fwd_kernel<1, OT><<<g, kBlock, 0, st>>>(b, nrhs, ld, perm, n_b, xhat); break;
+    case 2: transform_fwd_kernel<2, OT><<<g, kBlock, 0, st>>>(b, nrhs, ld, perm, n_b, xhat); break;
+    case 3: transform_fwd_kernel<3, OT><<<g, kBlock, 0, st>>>(b, nrhs, ld, perm, n_b, xhat); break;
+    case 4: transform_fwd_kernel<4, OT><<<g, kBlock, 0, st>>>(b, nrhs, ld, perm, n_b, xhat); break;
+    default: fail(AMGSYM_ERR_ARG, "the device transform supports s <= 4");
+  }
+}
+
+void launch_transform_fwd(const double* b, int32_t nrhs, int64_t ld, const int32_t* perm, int64_t n_b, int32_t s,
+                          void* xhat, VecType ot, cudaStream_t st) {
+  if (ot == VEC_F64)
+    fwd_dispatch<double>(b, nrhs, ld, perm, n_b, s, static_cast<double*>(xhat), st);
+  else
+    fwd_dispatch<float>(b, nrhs, ld, perm, n_b, s, static_cast<float*>(xhat), st);
+}
+
+template <typename IT>
+static void bwd_dispatch(const IT* xhat, int32_t nrhs, const int32_t* perm, int64_t n_b, int32_t s, double* x,
+                         int64_t ld, cudaStream_t st) {
+  const int g = grid_for(n_b * nrhs, kBlock);
+  switch (s) {
+    case 0: transform_bwd_kernel<0, IT><<<g, kBlock, 0, st>>>(xhat, nrhs, perm, n_b, x, ld); break;
+    case 1: transform_bwd_kernel<1, IT><<<g, kBlock, 0, st>>>(xhat, nrhs, perm, n_b, x, ld); break;
+    case 2: transform_bwd_kernel<2, IT><<<g, kBlock, 0, st>>>(xhat, nrhs, perm, n_b, x, ld); break;
+    case 3: transform_bwd_kernel<3, IT><<<g, kBlock, 0, st>>>(xhat, nrhs, perm, n_b, x, ld); break;
+    case 4: transform_bwd_kernel<4, IT><<<g, kBlock, 0, st>>>(xhat, nrhs, perm, n_b, x, ld); break;
+    default: fail(AMGSYM_ERR_ARG, "the device transform supports s <= 4");
+  }
+}
+
+void launch_transform_bwd(const void* xhat, VecType it, int32_t nrhs, const int32_t* perm, int64_t n_b, int32_t s,
+                          double* x, int64_t ld, cudaStream_t st) {
+  if (it == VEC_F64)
+    bwd_dispatch<double>(static_cast<const double*>(xhat), nrhs, perm, n_b, s, x, ld, st);
+  else
+    bwd_dispatch<float>(static_cast<const float*>(xhat), nrhs, perm, n_b, s, x, ld, st);
+}
+
+// ---------------------------------------------------------------------------
+// PCG updates.  Element e of a [rows][C] array belongs to column e % C; the
+// thread mapping is the SpMM's (thread owns CPT columns of a row slot) so the
+// fused dot reduction is shared.
+
+template <typename T>
+struct DotAcc {
+  using type = float;
+};
+template <>
+struct DotAcc<double> {
+  using type = double;
+};
+
+template <typename T, int CPT, bool HAS_DOT>
+__global__ void __launch_bounds__(kBlock) cg_update1_kernel(int64_t rows, int32_t C, T* __restrict__ x,
+                                                            T* __restrict__ r, const T* __restrict__ p,
+                                                            const T* __restrict__ q, DotArgs dot) {
+  using DT = typename DotAcc<T>::type;
+  const int TPR = C / CPT;
+  const int rows_pb = kBlock / TPR;
+  const int rloc = threadIdx.x / TPR;
+  const int c0 = (threadIdx.x % TPR) * CPT;
+  const bool has_cols = rloc < rows_pb;
+  double al[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) al[k] = dot.sc.alpha[c0 + k];
+  DT part[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) part[k] = (DT)0;
+  if (has_cols) {
+    for (int64_t row = blockIdx.x * (int64_t)rows_pb + rloc; row < rows; row += (int64_t)gridDim.x * rows_pb) {
+      const int64_t o = row * C + c0;
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        const T a = (T)al[k];
+        x[o + k] = x[o + k] + a * p[o + k];
+        const T rn = r[o + k] - a * q[o + k];
+        r[o + k] = rn;
+        part[k] += (DT)rn * (DT)rn;
+      }
+    }
+  }
+  if (HAS_DOT) {
+    __shared__ double sm[kBlock * CPT + 2 * kBlock];
+    double pd[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) pd[k] = (double)part[k];
+    block_dot<CPT>(dot, pd, c0, has_cols, rloc, rows_pb, C, sm);
+  }
+}
+
+template <typename T>
+static void update1_t(int64_t rows, int32_t C, void* x, void* r, const void* p, const void* q, const DotArgs& dot,
+                      cudaStream_t st) {
+  int g = grid_for(rows, kBlock / C > 0 ? kBlock / C : 1);
+  if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
+  cg_update1_kernel<T, 1, true><<<g, kBlock, 0, st>>>(rows, C, static_cast<T*>(x), static_cast<T*>(r),
+                                                      static_cast<const T*>(p), static_cast<const T*>(q), dot);
+}
+
+void launch_cg_update1(VecType vt, int64_t rows, int32_t C, void* x, void* r, const void* p, const void* q,
+                       const DotArgs& dot, cudaStream_t st) {
+  if (vt == VEC_F64)
+    update1_t<double>(rows, C, x, r, p, q, dot, st);
+  else
+    update1_t<float>(rows, C, x, r, p, q, dot, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) cg_update2_kernel(int64_t count, int32_t C, T* __restrict__ p,
+                                                            const T* __restrict__ z, const double* __restrict__ beta) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const T b = (T)beta[e % C];
+    p[e] = z[e] + b * p[e];
+  }
+}
+
+void launch_cg_update2(VecType vt, int64_t rows, int32_t C, void* p, const void* z, const double* beta,
+                       cudaStream_t st) {
+  const int64_t count = rows * C;
+  const int g = grid_for(count, kBlock);
+  if (vt == VEC_F64)
+    cg_update2_kernel<double><<<g, kBlock, 0, st>>>(count, C, static_cast<double*>(p), static_cast<const double*>(z), beta);
+  else
+    cg_update2_kernel<float><<<g, kBlock, 0, st>>>(count, C, static_cast<float*>(p), static_cast<const float*>(z), beta);
+}
+
+template <typename T>
+__global__ void add_to_f64_kernel(int64_t count, double* __restrict__ y, const T* __restrict__ x) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] += (double)x[e];
+}
+
+void launch_add_to_f64(VecType xt, int64_t count, double* y, const void* x, cudaStream_t st) {
+  const int g = grid_for(count, kBlock);
+  if (xt == VEC_F64)
+    add_to_f64_kernel<double><<<g, kBlock, 0, st>>>(count, y, static_cast<const double*>(x));
+  else
+    add_to_f64_kernel<float><<<g, kBlock, 0, st>>>(count, y, static_cast<const float*>(x));
+}
+
+template <typename T>
+__global__ void copy_kernel(int64_t count, T* __restrict__ d, const T* __restrict__ s) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = s[e];
+}
+
+void launch_copy(VecType vt, int64_t count, void* dst, const void* src, cudaStream_t st) {
+  const int g = grid_for(count, kBlock);
+  if (vt == VEC_F64)
+    copy_kernel<double><<<g, kBlock, 0, st>>>(count, static_cast<double*>(dst), static_cast<const double*>(src));
+  else
+    copy_kernel<float><<<g, kBlock, 0, st>>>(count, static_cast<float*>(dst), static_cast<const float*>(src));
+}
+
+template <typename T>
+__global__ void zero_kernel(int64_t count, T* __restrict__ d) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (T)0;
+}
+
+void launch_zero(VecType vt, int64_t count, void* dst, cudaStream_t st) {
+  const int g = grid_for(count, kBlock);
+  if (vt == VEC_F64)
+    zero_kernel<double><<<g, kBlock, 0, st>>>(count, static_cast<double*>(dst));
+  else
+    zero_kernel<float><<<g, kBlock, 0, st>>>(count, static_cast<float*>(dst));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) dot_kernel(int64_t rows, int32_t C, const T* __restrict__ a,
+                                                     const T* __restrict__ b, DotArgs dot) {
+  const int TPR = C;
+  const int rows_pb = kBlock / TPR;
+  const int rloc = threadIdx.x / TPR;
+  const int c0 = threadIdx.x % TPR;
+  const bool has_cols = rloc < rows_pb;
+  double part[1] = {0.0};
+  if (has_cols)
+    for (int64_t row = blockIdx.x * (int64_t)rows_pb + rloc; row < rows; row += (int64_t)gridDim.x * rows_pb)
+      part[0] += (double)a[row * C + c0] * (double)b[row * C + c0];
+  __shared__ double sm[kBlock + 2 * kBlock];
+  block_dot<1>(dot, part, c0, has_cols, rloc, rows_pb, C, sm);
+}
+
+void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,
+                cudaStream_t st) {
+  int g = grid_for(rows, kBlock / C > 0 ? kBlock / C : 1);
+  if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
+  if (vt == VEC_F64)
+    dot_kernel<double><<<g, kBlock, 0, st>>>(rows, C, static_cast<const double*>(a), static_cast<const double*>(b), dot);
+  else
+    dot_kernel<float><<<g, kBlock, 0, st>>>(rows, C, static_cast<const float*>(a), static_cast<const float*>(b), dot);
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level (Sec. 5: "a direct method solves the coarsest level"):
+// Z = A_c^{-1} Y with the precomputed FP64 inverse; FP64 arithmetic.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) coarse_kernel(int32_t n, int32_t C, const double* __restrict__ Ainv,
+                                                        const T* __restrict__ Y, T* __restrict__ Z) {
+  const int64_t total = (int64_t)n * C;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / C, c = t - i * C;
+    const double* a = Ainv + i * n;
+    double acc0 = 0.0, acc1 = 0.0;
+    int j = 0;
+    for (; j + 1 < n; j += 2) {
+      acc0 = fma(a[j], (double)Y[(int64_t)j * C + c], acc0);
+      acc1 = fma(a[j + 1], (double)Y[(int64_t)(j + 1) * C + c], acc1);
+    }
+    if (j < n) acc0 = fma(a[j], (double)Y[(int64_t)j * C + c], acc0);
+    Z[t] = (T)(acc0 + acc1);
+  }
+}
+
+void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
+                         cudaStream_t st) {
+  const int64_t total = (int64_t)n * C;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 63) / 64, max_grid_blocks()));
+  if (vt == VEC_F64)
+    coarse_kernel<double><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const double*>(Y), static_cast<double*>(Z));
+  else
+    coarse_kernel<float><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const float*>(Y), static_cast<float*>(Z));
+}
+
+__global__ void init_scalars_kernel(DevScalars sc, int32_t nrhs, int32_t nb) {
+  __shared__ int n_act;
+  if (threadIdx.x == 0) n_act = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < nrhs * nb; c += blockDim.x) {
+    const int r = c / nb;
+    const int act = sc.bnorm2[r] > 0.0 ? 1 : 0;
+    sc.active[c] = act;
+    sc.alpha[c] = 0.0;
+    sc.beta[c] = 0.0;
+    sc.rz[c] = 0.0;
+    sc.rr[c] = 0.0;
+    if (act && (c % nb) == 0) atomicAdd(&n_act, 1);
+  }
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) sc.relres[r] = sc.bnorm2[r] > 0.0 ? 1.0 : 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sc.status[0] = n_act;
+    sc.status[1] = 0;
+    sc.status[2] = 0;
+    *sc.ticket = 0u;
+  }
+}
+
+void launch_init_scalars(const DevScalars& sc, int32_t nrhs, int32_t nb, cudaStream_t st) {
+  init_scalars_kernel<<<1, kBlock, 0, st>>>(sc, nrhs, nb);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint coefficient gradient (see amgsym_fv_grad_logk): one thread per cell,
+// both faces of every axis, FP64.
+struct GridDev {
+  int32_t d;
+  int64_t N[3];
+  int64_t off[3];
+};
+
+__global__ void __launch_bounds__(kBlock) fv_grad_kernel(GridDev g, const double* __restrict__ w,
+                                                         const double* __restrict__ k, const double* __restrict__ u,
+                                                         const double* __restrict__ lam, int32_t nrhs, int64_t ld,
+                                                         double* __restrict__ grad, int32_t accumulate) {
+  const int64_t n = g.N[0] * g.N[1] * g.N[2];
+  const int64_t stride[3] = {1, g.N[0], g.N[0] * g.N[1]};
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c[3];
+    c[0] = p % g.N[0];
+    c[1] = (p / g.N[0]) % g.N[1];
+    c[2] = p / (g.N[0] * g.N[1]);
+    const double kp = k[p];
+    double acc = 0.0;
+    for (int a = 0; a < g.d; ++a) {
+      double area = 1.0;
+      for (int b = 0; b < g.d; ++b)
+        if (b != a) area *= w[g.off[b] + c[b]];
+      const double hp = w[g.off[a] + c[a]];
+      const double rp = hp / (2.0 * kp);
+      const double dtdg_fac = hp / (2.0 * area * kp);  // dt/dg_p = t^2 * this
+      for (int side = 0; side < 2; ++side) {
+        const bool interior = side == 0 ? c[a] > 0 : c[a] < g.N[a] - 1;
+        double t;
+        int64_t q = -1;
+        if (interior) {
+          q = side == 0 ? p - stride[a] : p + stride[a];
+          const double hq = w[g.off[a] + c[a] + (side == 0 ? -1 : 1)];
+          t = area / (rp + hq / (2.0 * k[q]));
+        } else {
+          t = area / rp;
+        }
+        double dLdt = 0.0;
+        for (int r = 0; r < nrhs; ++r) {
+          const double up = u[r * ld + p], lp = lam[r * ld + p];
+          if (interior)
+            dLdt -= (lp - lam[r * ld + q]) * (up - u[r * ld + q]);
+          else
+            dLdt -= lp * up;
+        }
+        acc += dLdt * t * t * dtdg_fac;
+      }
+    }
+    grad[p] = accumulate ? grad[p] + acc : acc;
+  }
+}
+
+void launch_fv_grad(int32_t d, const int64_t* N, const double* widths, const double* k, const double* u,
+                    const double* lam, int32_t nrhs, int64_t ld, double* grad, int32_t accumulate,
+                    cudaStream_t st) {
+  GridDev g;
+  g.d = d;
+  int64_t off = 0;
+  for (int a = 0; a < 3; ++a) {
+    g.N[a] = a < d ? N[a] : 1;
+    g.off[a] = off;
+    if (a < d) off += N[a];
+  }
+  const int64_t n = g.N[0] * g.N[1] * g.N[2];
+  fv_grad_kernel<<<grid_for(n, kBlock), kBlock, 0, st>>>(g, widths, k, u, lam, nrhs, ld, grad, accumulate);
+}
+
+}  // namespace amgsym

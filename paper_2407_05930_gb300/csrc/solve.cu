@@ -1,0 +1,693 @@
+// Device residency of a problem and the solve of Alg. 1 ("symsolver"):
+// forward transform, 2^s decoupled PCG solves run as one multi-column PCG
+// preconditioned by I (x) M_inn^{-1} (eqs. "AMGinn", "LRCAMG" with k = 0),
+// backward transform.  Optional FP64 iterative refinement around an FP32
+// inner PCG (mixed precision).  Every arithmetic step runs in the kernels of
+// k_spmm.cu / k_misc.cu; this file only allocates, uploads and sequences.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device.h"
+#include "internal.h"
+
+namespace amgsym {
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      fail(e_ == cudaErrorMemoryAllocation ? AMGSYM_ERR_OOM : AMGSYM_ERR_CUDA,            \
+           std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+static void check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) fail(AMGSYM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
+// Precision-specific work arrays for one column count.
+struct LevelWork {
+  void* y = nullptr;  // level rhs (levels >= 1)
+  void* z = nullptr;  // level solution (levels >= 1)
+  void* r = nullptr;  // residual
+  void* t = nullptr;  // smoother temporary
+};
+
+struct PrecWork {
+  bool ready = false;
+  std::vector<LevelWork> lw;
+  void *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;  // PCG vectors
+};
+
+struct GraphKey {
+  int mode = -1;
+  int32_t nrhs = 0;
+  double tol = 0.0;
+  bool operator==(const GraphKey& o) const { return mode == o.mode && nrhs == o.nrhs && tol == o.tol; }
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key;
+};
+
+struct Device {
+  int device_id = 0;
+  int precisions = 3;
+  int nu = 1;
+  int32_t s = 0, nb = 1;
+  int64_t n_b = 0;
+  DevCsr Ainn;  // alias of lv[0].A
+  DevIface iface;
+  int32_t* perm = nullptr;
+  std::vector<DevLevel> lv;
+  std::vector<void*> owned;  // setup allocations
+  // work arrays for work_nrhs right-hand sides
+  int32_t work_nrhs = 0;
+  std::vector<void*> work_owned;
+  double* bh = nullptr;  // b^ (FP64)
+  double* xh = nullptr;  // x^ (FP64)
+  PrecWork w64, w32;
+  DevScalars sc_out, sc_in;
+  int32_t* h_status = nullptr;  // pinned [2][4]
+  double* h_relres = nullptr;   // pinned [work_nrhs]
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  GraphCache graph;
+};
+
+template <typename T>
+static T* dalloc(std::vector<void*>& owner, int64_t count) {
+  if (count <= 0) return nullptr;
+  void* p = nullptr;
+  CK(cudaMalloc(&p, sizeof(T) * (size_t)count));
+  owner.push_back(p);
+  return static_cast<T*>(p);
+}
+
+template <typename T>
+static T* upload(std::vector<void*>& owner, const T* src, int64_t count) {
+  T* d = dalloc<T>(owner, count);
+  if (count > 0) CK(cudaMemcpy(d, src, sizeof(T) * (size_t)count, cudaMemcpyHostToDevice));
+  return d;
+}
+
+static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions) {
+  DevCsr D;
+  if (M.rows > INT32_MAX || M.nnz() > INT32_MAX) fail(AMGSYM_ERR_ARG, "matrix too large for 32-bit device indices");
+  D.rows = (int32_t)M.rows;
+  D.cols = (int32_t)M.cols;
+  D.nnz = M.nnz();
+  std::vector<int32_t> p32(M.ptr.begin(), M.ptr.end());
+  D.ptr = upload(owner, p32.data(), (int64_t)p32.size());
+  D.idx = upload(owner, M.idx.data(), D.nnz);
+  if (precisions & 1) D.v64 = upload(owner, M.val.data(), D.nnz);
+  if (precisions & 2) {
+    std::vector<float> v(M.val.begin(), M.val.end());
+    D.v32 = upload(owner, v.data(), D.nnz);
+  }
+  if (precisions & 4) {
+    std::vector<__nv_bfloat16> v(D.nnz);
+    for (int64_t i = 0; i < D.nnz; ++i) v[i] = __float2bfloat16((float)M.val[i]);
+    D.v16 = upload(owner, v.data(), D.nnz);
+  }
+  return D;
+}
+
+static void free_work(Device* D) {
+  for (void* p : D->work_owned) cudaFree(p);
+  D->work_owned.clear();
+  if (D->h_status) cudaFreeHost(D->h_status);
+  if (D->h_relres) cudaFreeHost(D->h_relres);
+  D->h_status = nullptr;
+  D->h_relres = nullptr;
+  D->w64 = PrecWork();
+  D->w32 = PrecWork();
+  D->work_nrhs = 0;
+  if (D->graph.exec) cudaGraphExecDestroy(D->graph.exec);
+  D->graph = GraphCache();
+}
+
+void device_free(amgsym_problem* p) {
+  Device* D = p->dev;
+  if (!D) return;
+  cudaSetDevice(D->device_id);
+  cudaDeviceSynchronize();
+  free_work(D);
+  for (void* q : D->owned) cudaFree(q);
+  if (D->cap_stream) cudaStreamDestroy(D->cap_stream);
+  for (auto& e : D->ev)
+    if (e) cudaEventDestroy(e);
+  delete D;
+  p->dev = nullptr;
+}
+
+void device_upload(amgsym_problem* p) {
+  device_free(p);
+  auto* D = new Device();
+  p->dev = D;
+  CK(cudaGetDevice(&D->device_id));
+  D->precisions = p->opts.precisions | 1;  // FP64 operator always (outer residuals)
+  D->nu = p->opts.nu;
+  D->s = p->s;
+  D->nb = p->nb;
+  D->n_b = p->n_b;
+  if (p->s > 4) fail(AMGSYM_ERR_ARG, "device path supports s <= 4");
+  D->perm = upload(D->owned, p->perm.data(), (int64_t)p->perm.size());
+  const auto& H = p->H;
+  D->lv.resize(H.levels.size());
+  for (size_t l = 0; l < H.levels.size(); ++l) {
+    const HostLevel& L = H.levels[l];
+    DevLevel& V = D->lv[l];
+    V.n = (int32_t)L.A.rows;
+    V.omega = L.omega;
+    // level 0 keeps FP64 always (the reduced operator of the outer loop)
+    V.A = upload_csr(D->owned, L.A, l == 0 ? D->precisions : p->opts.precisions);
+    if (!L.coarse_inv.empty()) {
+      V.cinv = upload(D->owned, L.coarse_inv.data(), (int64_t)L.coarse_inv.size());
+    } else {
+      V.P = upload_csr(D->owned, L.P, p->opts.precisions);
+      V.R = upload_csr(D->owned, L.R, p->opts.precisions);
+      V.G = upload_csr(D->owned, L.G, p->opts.precisions);
+      V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions);
+    }
+  }
+  D->Ainn = D->lv[0].A;
+  // interface couplings
+  const int64_t ne = (int64_t)p->irow.size();
+  if (ne > 0) {
+    const int64_t words = (p->n_b + 31) / 32;
+    std::vector<uint32_t> mask(words, 0);
+    std::vector<int32_t> prefix(words, 0), iptr;
+    for (int64_t e = 0; e < ne; ++e) {
+      const int32_t r = p->irow[e];
+      if (e == 0 || p->irow[e - 1] != r) {
+        mask[r >> 5] |= 1u << (r & 31);
+        iptr.push_back((int32_t)e);
+      }
+    }
+    iptr.push_back((int32_t)ne);
+    int32_t run = 0;
+    for (int64_t w = 0; w < words; ++w) {
+      prefix[w] = run;
+      run += __builtin_popcount(mask[w]);
+    }
+    D->iface.n_rows_flagged = run;
+    D->iface.n_entries = ne;
+    D->iface.mask = upload(D->owned, mask.data(), words);
+    D->iface.prefix = upload(D->owned, prefix.data(), words);
+    D->iface.iptr = upload(D->owned, iptr.data(), (int64_t)iptr.size());
+    D->iface.icol = upload(D->owned, p->icol.data(), ne);
+    D->iface.ival64 = upload(D->owned, p->ivals.data(), ne * p->nb);
+    std::vector<float> v32(p->ivals.begin(), p->ivals.end());
+    D->iface.ival32 = upload(D->owned, v32.data(), ne * p->nb);
+  }
+  CK(cudaStreamCreateWithFlags(&D->cap_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&D->ev[0], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&D->ev[1], cudaEventDisableTiming));
+  CK(cudaDeviceSynchronize());
+}
+
+static void alloc_scalars(Device* D, DevScalars& sc, int32_t C, int32_t nrhs) {
+  sc.rz = dalloc<double>(D->work_owned, C);
+  sc.alpha = dalloc<double>(D->work_owned, C);
+  sc.beta = dalloc<double>(D->work_owned, C);
+  sc.rr = dalloc<double>(D->work_owned, C);
+  sc.bnorm2 = dalloc<double>(D->work_owned, nrhs);
+  sc.relres = dalloc<double>(D->work_owned, nrhs);
+  sc.active = dalloc<int32_t>(D->work_owned, C);
+  sc.status = dalloc<int32_t>(D->work_owned, 4);
+  sc.partial_cap = (int64_t)max_grid_blocks() * C;
+  sc.partials = dalloc<double>(D->work_owned, sc.partial_cap);
+  sc.ticket = dalloc<unsigned>(D->work_owned, 1);
+  CK(cudaMemset(sc.ticket, 0, sizeof(unsigned)));
+  CK(cudaMemset(sc.status, 0, 4 * sizeof(int32_t)));
+}
+
+static void ensure_work(Device* D, int32_t nrhs, VecType vt) {
+  if (nrhs > D->work_nrhs) {
+    CK(cudaDeviceSynchronize());
+    free_work(D);
+    D->work_nrhs = nrhs;
+    const int32_t C = nrhs * D->nb;
+    D->bh = dalloc<double>(D->work_owned, D->n_b * C);
+    D->xh = dalloc<double>(D->work_owned, D->n_b * C);
+    alloc_scalars(D, D->sc_out, C, nrhs);
+    alloc_scalars(D, D->sc_in, C, nrhs);
+    CK(cudaMallocHost(&D->h_status, 8 * sizeof(int32_t)));
+    CK(cudaMallocHost(&D->h_relres, sizeof(double) * nrhs));
+  }
+  PrecWork& W = vt == VEC_F64 ? D->w64 : D->w32;
+  if (W.ready) return;
+  const int32_t C = D->work_nrhs * D->nb;
+  const size_t es = vt == VEC_F64 ? 8 : 4;
+  auto vec = [&](int64_t rows) -> void* {
+    void* p = nullptr;
+    if (rows <= 0) return nullptr;
+    CK(cudaMalloc(&p, es * (size_t)rows * (size_t)C));
+    D->work_owned.push_back(p);
+    return p;
+  };
+  W.lw.resize(D->lv.size());
+  for (size_t l = 0; l < D->lv.size(); ++l) {
+    const int64_t n = D->lv[l].n;
+    if (l > 0) {
+      W.lw[l].y = vec(n);
+      W.lw[l].z = vec(n);
+    }
+    W.lw[l].r = vec(n);
+    W.lw[l].t = vec(n);
+  }
+  W.r = vec(D->n_b);
+  W.z = vec(D->n_b);
+  W.p = vec(D->n_b);
+  W.q = vec(D->n_b);
+  // FP64 PCG iterates on x^ itself; the FP32 inner PCG on its own correction.
+  W.x = vt == VEC_F64 ? (void*)D->xh : vec(D->n_b);
+  W.ready = true;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel sequencing.
+
+struct Ctx {
+  Device* D;
+  int32_t C;
+  VecType vt;       // vector precision of the V-cycle / inner PCG
+  ValType mt;       // matrix value precision of the V-cycle
+  bool finest_hat;  // V-cycle level-0 residual with A^_i
+  cudaStream_t st;
+};
+
+static void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X, void* Y,
+                 double alpha, double beta, const void* Z, bool iface, const DotArgs* dot) {
+  SpmmArgs a;
+  a.rows = M.rows;
+  a.C = c.C;
+  a.ptr = M.ptr;
+  a.idx = M.idx;
+  a.val = M.vals(mt);
+  if (!a.val) fail(AMGSYM_ERR_STATE, "matrix values of the requested precision were not built (opts.precisions)");
+  a.X = X;
+  a.Y = Y;
+  a.Z = Z;
+  a.alpha = alpha;
+  a.beta = beta;
+  if (iface && c.D->iface.mask) {
+    a.imask = c.D->iface.mask;
+    a.iprefix = c.D->iface.prefix;
+    a.iptr = c.D->iface.iptr;
+    a.icol = c.D->iface.icol;
+    const bool f64 = (mt == VAL_F64) || (xt == VEC_F64);
+    a.ival = f64 ? (const void*)c.D->iface.ival64 : (const void*)c.D->iface.ival32;
+    a.nb = c.D->nb;
+  }
+  if (dot) a.dot = *dot;
+  launch_spmm(mt, xt, ot, a, c.st);
+  check_launch();
+}
+
+// One V(nu, nu) cycle at level l: z = M_l^{-1} y (Alg. "apply" shape with the
+// A_inn hierarchy; presmoothing from zero).  `last` is the optional fused dot
+// of the final level-0 kernel.
+static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* last) {
+  Device* D = c.D;
+  const DevLevel& L = D->lv[l];
+  PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
+  LevelWork& lw = W.lw[l];
+  if (L.cinv) {
+    launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st);
+    check_launch();
+    if (last) {
+      launch_dot(c.vt, L.n, c.C, last->W, z, *last, c.st);
+      check_launch();
+    }
+    return;
+  }
+  const bool hat = c.finest_hat && l == 0;
+  const ValType mt = c.mt;
+  const VecType vt = c.vt;
+  // presmoothing: the first sweep from zero is z = w G^T G y
+  spmm(c, L.G, mt, vt, vt, y, lw.t, 1.0, 0.0, nullptr, false, nullptr);
+  spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 0.0, nullptr, false, nullptr);
+  for (int k = 1; k < D->nu; ++k) {
+    spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+    spmm(c, L.G, mt, vt, vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 1.0, z, false, nullptr);
+  }
+  // residual and restriction r_c = P^T (y - A z)
+  spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+  LevelWork& cw = W.lw[l + 1];
+  spmm(c, L.R, mt, vt, vt, lw.r, cw.y, 1.0, 0.0, nullptr, false, nullptr);
+  vcycle(c, l + 1, cw.y, cw.z, nullptr);
+  // prolongation and update z += P z_c
+  spmm(c, L.P, mt, vt, vt, cw.z, z, 1.0, 1.0, z, false, nullptr);
+  // postsmoothing
+  for (int k = 0; k < D->nu; ++k) {
+    spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+    spmm(c, L.G, mt, vt, vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 1.0, z, false, k == D->nu - 1 ? last : nullptr);
+  }
+}
+
+static DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb,
+                        double tol, int count_iter) {
+  DotArgs d;
+  d.mode = mode;
+  d.final = final;
+  d.W = W;
+  d.sc = sc;
+  d.cp.tol2 = tol * tol;
+  d.cp.nrhs = nrhs;
+  d.cp.nb = nb;
+  d.cp.count_iter = count_iter;
+  return d;
+}
+
+// One PCG iteration on vectors of W (precision c.vt):
+// q = A^ p (alpha), x += alpha p, r -= alpha q (convergence), z = M r (beta), p = z + beta p.
+static void pcg_iteration(const Ctx& c, PrecWork& W, const DevScalars& sc, int32_t nrhs, double tol) {
+  Device* D = c.D;
+  const ValType kmt = c.vt == VEC_F64 ? VAL_F64 : VAL_F32;  // reduced operator precision
+  DotArgs dpq = make_dot(sc, DOT_WY, FIN_ALPHA, W.p, nrhs, D->nb, tol, 0);
+  spmm(c, D->Ainn, kmt, c.vt, c.vt, W.p, W.q, 1.0, 0.0, nullptr, true, &dpq);
+  DotArgs drr = make_dot(sc, DOT_YY, FIN_CONV, nullptr, nrhs, D->nb, tol, 1);
+  launch_cg_update1(c.vt, D->n_b, c.C, W.x, W.r, W.p, W.q, drr, c.st);
+  check_launch();
+  DotArgs drz = make_dot(sc, DOT_WY, FIN_BETA, W.r, nrhs, D->nb, tol, 0);
+  vcycle(c, 0, W.r, W.z, &drz);
+  launch_cg_update2(c.vt, D->n_b, c.C, W.p, W.z, sc.beta, c.st);
+  check_launch();
+}
+
+static void read_status(Device* D, const DevScalars& sc, cudaStream_t st, int32_t* out4) {
+  CK(cudaMemcpyAsync(D->h_status, sc.status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::memcpy(out4, D->h_status, 4 * sizeof(int32_t));
+}
+
+// PCG loop until every RHS of `sc` is inactive or maxit; returns iterations.
+// The host checks the status of iteration k while iteration k + 1 runs.
+static int pcg_loop(const Ctx& c, PrecWork& W, const DevScalars& sc, int32_t nrhs, double tol, int maxit,
+                    bool use_graph, int graph_mode, bool* breakdown) {
+  GraphKey graph_key;
+  graph_key.mode = graph_mode;
+  graph_key.nrhs = nrhs;
+  graph_key.tol = tol;
+  Device* D = c.D;
+  // start: z = M r, rz, p = z
+  DotArgs drz = make_dot(sc, DOT_WY, FIN_STORE_RZ, W.r, nrhs, D->nb, tol, 0);
+  vcycle(c, 0, W.r, W.z, &drz);
+  launch_copy(c.vt, D->n_b * c.C, W.p, W.z, c.st);
+  check_launch();
+  cudaGraphExec_t exec = nullptr;
+  if (use_graph) {
+    if (D->graph.exec && D->graph.key == graph_key) {
+      exec = D->graph.exec;
+    } else {
+      if (D->graph.exec) cudaGraphExecDestroy(D->graph.exec);
+      D->graph = GraphCache();
+      Ctx cc = c;
+      cc.st = D->cap_stream;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(D->cap_stream, cudaStreamCaptureModeThreadLocal));
+      try {
+        pcg_iteration(cc, W, sc, nrhs, tol);
+        CK(cudaMemcpyAsync(D->h_status, sc.status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, D->cap_stream));
+      } catch (...) {
+        cudaStreamEndCapture(D->cap_stream, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      CK(cudaStreamEndCapture(D->cap_stream, &g));
+      CK(cudaGraphInstantiate(&exec, g, 0));
+      cudaGraphDestroy(g);
+      D->graph.exec = exec;
+      D->graph.key = graph_key;
+    }
+  }
+  // Two status slots so the copy of iteration k is not overwritten by k+1
+  // before the host reads it: slot = k % 2 (graph path writes slot 0 only,
+  // so it synchronises per iteration via the event).
+  int it = 0;
+  int done_at = -1;
+  *breakdown = false;
+  int32_t st4[4];
+  for (it = 0; it < maxit; ++it) {
+    if (exec) {
+      CK(cudaGraphLaunch(exec, c.st));
+      CK(cudaEventRecord(D->ev[0], c.st));
+      CK(cudaEventSynchronize(D->ev[0]));
+      std::memcpy(st4, D->h_status, sizeof(st4));
+    } else {
+      pcg_iteration(c, W, sc, nrhs, tol);
+      read_status(D, sc, c.st, st4);
+    }
+    if (st4[1]) {
+      *breakdown = true;
+      done_at = it + 1;
+      break;
+    }
+    if (st4[0] == 0) {
+      done_at = it + 1;
+      break;
+    }
+  }
+  return done_at < 0 ? maxit : done_at;
+}
+
+static void check_ptr(const void* p, const char* what) {
+  if (!p) fail(AMGSYM_ERR_ARG, std::string(what) + " is NULL");
+  if (((uintptr_t)p) % 16) fail(AMGSYM_ERR_ARG, std::string(what) + " must be 16-byte aligned");
+}
+
+static Device* require_dev(amgsym_t h) {
+  if (!h) fail(AMGSYM_ERR_ARG, "NULL handle");
+  if (!h->dev) fail(AMGSYM_ERR_STATE, "problem is not on the device (call amgsym_setup without host_only)");
+  CK(cudaSetDevice(h->dev->device_id));
+  return h->dev;
+}
+
+static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                                const amgsym_solve_opts* sopts, void* stream, amgsym_solve_info* info) {
+  Device* D = require_dev(h);
+  amgsym_solve_opts o;
+  amgsym_solve_opts_default(&o);
+  if (sopts) o = *sopts;
+  if (nrhs < 1) fail(AMGSYM_ERR_ARG, "nrhs must be >= 1");
+  if (ld < h->n) fail(AMGSYM_ERR_ARG, "ld must be >= n");
+  if (!b_dev || !x_dev) fail(AMGSYM_ERR_ARG, "NULL vector");
+  if ((int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be <= 256 per call");
+  if (!(o.tol > 0.0)) fail(AMGSYM_ERR_ARG, "tol must be positive");
+  if (o.maxit < 1) fail(AMGSYM_ERR_ARG, "maxit must be >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool mixed = o.precision != AMGSYM_PREC_FP64;
+  const VecType vt = mixed ? VEC_F32 : VEC_F64;
+  const ValType vmt = o.precision == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : mixed ? VAL_F32 : VAL_F64;
+  if (mixed && !(h->opts.precisions & (o.precision == AMGSYM_PREC_MIXED_BF16 ? 4 : 2)))
+    fail(AMGSYM_ERR_STATE, "setup did not build the value precision this mode needs (opts.precisions)");
+  ensure_work(D, nrhs, vt);
+  const int32_t C = nrhs * D->nb;
+  Ctx c{D, C, vt, vmt, o.finest_hat != 0, st};
+  Ctx c64{D, C, VEC_F64, VAL_F64, false, st};
+  // 64-bit work is needed for the FP64 path; the mixed path uses bh/xh only.
+  PrecWork& W = mixed ? D->w32 : D->w64;
+  // Forward transform and reference norms.
+  launch_transform_fwd(b_dev, nrhs, ld, D->perm, D->n_b, D->s, D->bh, VEC_F64, st);
+  check_launch();
+  DotArgs dbn = make_dot(D->sc_out, DOT_WY, FIN_STORE_BN, nullptr, nrhs, D->nb, o.tol, 0);
+  launch_dot(VEC_F64, D->n_b, C, D->bh, D->bh, dbn, st);
+  check_launch();
+  launch_init_scalars(D->sc_out, nrhs, D->nb, st);
+  check_launch();
+  if (o.use_x0) {
+    launch_transform_fwd(x_dev, nrhs, ld, D->perm, D->n_b, D->s, D->xh, VEC_F64, st);
+  } else {
+    launch_zero(VEC_F64, D->n_b * C, D->xh, st);
+  }
+  check_launch();
+  const bool graphs = o.use_graph != 0;
+  int total_it = 0, outer = 0;
+  bool breakdown = false;
+  int32_t st4[4];
+  amgsym_status result = AMGSYM_OK;
+  if (!mixed) {
+    // FP64 PCG with up to two restarts from the true residual (reading of
+    // the stopping rule: recurrence residual, confirmed by b^ - A^ x^).
+    for (int restart = 0; restart < 3; ++restart) {
+      launch_init_scalars(D->sc_out, nrhs, D->nb, st);
+      DotArgs drr = make_dot(D->sc_out, DOT_YY, FIN_CONV, nullptr, nrhs, D->nb, o.tol, 0);
+      spmm(c64, D->Ainn, VAL_F64, VEC_F64, VEC_F64, D->xh, W.r, -1.0, 1.0, D->bh, true, &drr);
+      read_status(D, D->sc_out, st, st4);
+      if (st4[0] == 0 || total_it >= o.maxit) break;
+      const int it = pcg_loop(c, W, D->sc_out, nrhs, o.tol, o.maxit - total_it, graphs,
+                              0x100 | (o.finest_hat ? 1 : 0), &breakdown);
+      total_it += it;
+      if (breakdown) break;
+    }
+    if (!breakdown) {
+      // final true residual
+      launch_init_scalars(D->sc_out, nrhs, D->nb, st);
+      DotArgs drr = make_dot(D->sc_out, DOT_YY, FIN_CONV, nullptr, nrhs, D->nb, o.tol, 0);
+      spmm(c64, D->Ainn, VAL_F64, VEC_F64, VEC_F64, D->xh, W.r, -1.0, 1.0, D->bh, true, &drr);
+      read_status(D, D->sc_out, st, st4);
+    }
+  } else {
+    // FP64 iterative refinement around the FP32 inner PCG.
+    for (outer = 0; outer <= o.max_outer; ++outer) {
+      DotArgs drr = make_dot(D->sc_out, DOT_YY, FIN_CONV, nullptr, nrhs, D->nb, o.tol, 0);
+      // r32 = float(b^ - A^ x^), FP64 arithmetic
+      spmm(c64, D->Ainn, VAL_F64, VEC_F64, VEC_F32, D->xh, W.r, -1.0, 1.0, D->bh, true, &drr);
+      read_status(D, D->sc_out, st, st4);
+      if (st4[0] == 0 || outer == o.max_outer || total_it >= o.maxit) break;
+      // inner reference norms ||r||^2 per RHS; inner active = outer active
+      DotArgs dbi = make_dot(D->sc_in, DOT_WY, FIN_STORE_BN, nullptr, nrhs, D->nb, o.inner_tol, 0);
+      launch_dot(VEC_F32, D->n_b, C, W.r, W.r, dbi, st);
+      check_launch();
+      launch_init_scalars(D->sc_in, nrhs, D->nb, st);
+      check_launch();
+      CK(cudaMemcpyAsync(D->sc_in.active, D->sc_out.active, sizeof(int32_t) * C, cudaMemcpyDeviceToDevice, st));
+      launch_zero(VEC_F32, D->n_b * C, W.x, st);
+      check_launch();
+      const int it = pcg_loop(c, W, D->sc_in, nrhs, o.inner_tol, o.maxit - total_it, graphs,
+                              0x200 | (o.precision == AMGSYM_PREC_MIXED_BF16 ? 2 : 0) | (o.finest_hat ? 1 : 0),
+                              &breakdown);
+      total_it += it;
+      launch_add_to_f64(VEC_F32, D->n_b * C, D->xh, W.x, st);
+      check_launch();
+      if (breakdown) break;
+    }
+  }
+  launch_transform_bwd(D->xh, VEC_F64, nrhs, D->perm, D->n_b, D->s, x_dev, ld, st);
+  check_launch();
+  if (breakdown) {
+    CK(cudaStreamSynchronize(st));
+    fail(AMGSYM_ERR_BREAKDOWN, "PCG breakdown (p^T A p <= 0 or not finite)");
+  }
+  const bool converged = st4[0] == 0;
+  if (!converged) result = AMGSYM_NOT_CONVERGED;
+  if (info) {
+    CK(cudaMemcpyAsync(D->h_relres, D->sc_out.relres, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    info->iters = total_it;
+    info->outer_iters = mixed ? outer : 0;
+    info->converged = converged ? 1 : 0;
+    if (info->relres) std::memcpy(info->relres, D->h_relres, sizeof(double) * nrhs);
+  }
+  return result;
+}
+
+}  // namespace amgsym
+
+using namespace amgsym;
+
+#define API_BEGIN try {
+#define API_END                                          \
+  }                                                      \
+  catch (const amgsym::Error& e) {                       \
+    amgsym::set_last_error(e.msg);                       \
+    return e.code;                                       \
+  }                                                      \
+  catch (const std::bad_alloc&) {                        \
+    amgsym::set_last_error("host allocation failed");    \
+    return AMGSYM_ERR_OOM;                               \
+  }                                                      \
+  return AMGSYM_OK;
+
+extern "C" amgsym_status amgsym_solve(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                                      const amgsym_solve_opts* sopts, void* stream, amgsym_solve_info* info) {
+  try {
+    return solve_impl(h, b_dev, x_dev, nrhs, ld, sopts, stream, info);
+  } catch (const amgsym::Error& e) {
+    amgsym::set_last_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    amgsym::set_last_error("host allocation failed");
+    return AMGSYM_ERR_OOM;
+  }
+}
+
+extern "C" amgsym_status amgsym_solve_adjoint(amgsym_t h, const double* g_dev, double* lam_dev, int32_t nrhs,
+                                              int64_t ld, const amgsym_solve_opts* sopts, void* stream,
+                                              amgsym_solve_info* info) {
+  // A is symmetric (validated at creation), so A^T lambda = g is the same solve.
+  return amgsym_solve(h, g_dev, lam_dev, nrhs, ld, sopts, stream, info);
+}
+
+extern "C" amgsym_status amgsym_transform_forward(amgsym_t h, const double* b_dev, int32_t nrhs, int64_t ld,
+                                                  double* xhat_dev, void* stream) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (nrhs < 1 || ld < h->n || !b_dev || !xhat_dev) fail(AMGSYM_ERR_ARG, "bad arguments");
+  launch_transform_fwd(b_dev, nrhs, ld, D->perm, D->n_b, D->s, xhat_dev, VEC_F64, (cudaStream_t)stream);
+  check_launch();
+  API_END
+}
+
+extern "C" amgsym_status amgsym_transform_backward(amgsym_t h, const double* xhat_dev, int32_t nrhs,
+                                                   double* x_dev, int64_t ld, void* stream) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (nrhs < 1 || ld < h->n || !xhat_dev || !x_dev) fail(AMGSYM_ERR_ARG, "bad arguments");
+  launch_transform_bwd(xhat_dev, VEC_F64, nrhs, D->perm, D->n_b, D->s, x_dev, ld, (cudaStream_t)stream);
+  check_launch();
+  API_END
+}
+
+extern "C" amgsym_status amgsym_apply_reduced(amgsym_t h, const void* X_dev, void* Y_dev, int32_t nrhs,
+                                              int32_t prec, void* stream) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (nrhs < 1 || (int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
+  check_ptr(X_dev, "X");
+  check_ptr(Y_dev, "Y");
+  if (X_dev == Y_dev) fail(AMGSYM_ERR_ARG, "X and Y must not overlap");
+  const bool f64 = prec == AMGSYM_PREC_FP64;
+  const VecType vt = f64 ? VEC_F64 : VEC_F32;
+  const ValType mt = f64 ? VAL_F64 : VAL_F32;
+  if (!D->Ainn.vals(mt)) fail(AMGSYM_ERR_STATE, "value precision not built");
+  Ctx c{D, nrhs * D->nb, vt, mt, false, (cudaStream_t)stream};
+  spmm(c, D->Ainn, mt, vt, vt, X_dev, Y_dev, 1.0, 0.0, nullptr, true, nullptr);
+  API_END
+}
+
+extern "C" amgsym_status amgsym_vcycle(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs, int32_t prec,
+                                       int32_t finest_hat, void* stream) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (nrhs < 1 || (int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
+  check_ptr(R_dev, "R");
+  check_ptr(Z_dev, "Z");
+  if (R_dev == Z_dev) fail(AMGSYM_ERR_ARG, "R and Z must not overlap");
+  const bool f64 = prec == AMGSYM_PREC_FP64;
+  const VecType vt = f64 ? VEC_F64 : VEC_F32;
+  const ValType mt = f64 ? VAL_F64 : prec == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : VAL_F32;
+  ensure_work(D, nrhs, vt);
+  Ctx c{D, nrhs * D->nb, vt, mt, finest_hat != 0, (cudaStream_t)stream};
+  vcycle(c, 0, R_dev, Z_dev, nullptr);
+  API_END
+}
+
+extern "C" amgsym_status amgsym_fv_grad_logk(int32_t d, const int64_t* N, const double* widths_dev,
+                                             const double* k_dev, const double* u_dev, const double* lam_dev,
+                                             int32_t nrhs, int64_t ld, double* grad_dev, int32_t accumulate,
+                                             void* stream) {
+  API_BEGIN
+  if (d < 1 || d > 3 || !N) fail(AMGSYM_ERR_ARG, "grid dimension must be 1..3");
+  int64_t n = 1;
+  for (int a = 0; a < d; ++a) {
+    if (N[a] <= 0) fail(AMGSYM_ERR_ARG, "grid extent must be positive");
+    n *= N[a];
+  }
+  if (!widths_dev || !k_dev || !u_dev || !lam_dev || !grad_dev) fail(AMGSYM_ERR_ARG, "NULL argument");
+  if (nrhs < 1 || ld < n) fail(AMGSYM_ERR_ARG, "bad nrhs / ld");
+  launch_fv_grad(d, N, widths_dev, k_dev, u_dev, lam_dev, nrhs, ld, grad_dev, accumulate, (cudaStream_t)stream);
+  check_launch();
+  API_END
+}

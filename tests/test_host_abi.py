@@ -1,0 +1,167 @@
+"""Host-side logic of the C ABI (CPU only, no CUDA call).
+
+* every symbol declared in include/amgsym.h is exported by libamgsym.so;
+* the library's structured-grid generator and mirror map agree with the
+  oracle (map bit-exact, matrix to rounding);
+* create_problem validates the map and the block structure of eq.
+  "struct_2sym", and extracts A_inn and A_out,i equal to the oracle's blocks;
+* the AMG hierarchy has the structure the V-cycle relies on.
+"""
+
+import ctypes
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import paper_2407_05930_gb300 as amg
+from oracle import fv, grid, symmetry, transform
+from synth import gaussian_logk
+
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_header_symbols_exported():
+    hdr = open(os.path.join(ROOT, "include", "amgsym.h")).read()
+    names = set(re.findall(r"\b(amgsym_[a-z_0-9]+)\s*\(", hdr))
+    assert names, "no declarations found"
+    lib = ctypes.CDLL(amg.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(amg.EXPORTED) <= names
+
+
+@pytest.mark.parametrize("N,gamma", [((64,), 0.0), ((10, 8), 1.5), ((6, 8, 4), 1.5), ((256,), 1.5)])
+def test_generator_matches_oracle(N, gamma):
+    w = [amg.grid_widths(n, gamma) for n in N]
+    h = grid.widths(N, gamma)
+    for a, b in zip(w, h):
+        assert np.max(np.abs(a - b)) <= 4e-16
+        if a.size % 2 == 0:
+            assert np.array_equal(a, a[::-1])
+    rng = np.random.default_rng(0)
+    k = np.exp(rng.standard_normal(int(np.prod(N))))
+    rp, ci, v = amg.fv_assemble(N, w, k)
+    Ap = sp.csr_matrix((v, ci, rp), shape=(k.size, k.size))
+    Ao = fv.assemble(h, k)
+    assert (Ap != 0).nnz == Ao.nnz
+    # entrywise relative agreement: the widths are differences of nodes near
+    # 1/2, so one ulp of tanh becomes ~1e-13 relative in a wall-cell width
+    D = (Ap - Ao).tocoo()
+    ref = np.asarray(abs(Ao)[D.row, D.col]).ravel()
+    assert np.all(np.abs(D.data) <= 1e-12 * ref)
+
+
+@pytest.mark.parametrize("N,s", [((8, 6), 1), ((8, 8), 2), ((6, 4, 8), 3), ((4, 6, 2), 2), ((10,), 1), ((6, 4, 4), 0)])
+def test_mirror_perm_bit_exact(N, s):
+    assert np.array_equal(amg.mirror_perm(N, s), symmetry.mirror_perm(N, s))
+
+
+def _oracle_problem(N, s, gamma=1.5, seed=2):
+    g = gaussian_logk(N, s, seed=seed, corr=1.5)
+    h, k, A = fv.grid_operator(N, gamma, g)
+    return g, A
+
+
+@pytest.mark.parametrize("N,s", [((8, 6), 1), ((6, 8, 4), 3), ((8, 4, 6), 2)])
+def test_create_problem_extracts_oracle_blocks(N, s):
+    g, A = _oracle_problem(N, s)
+    perm = symmetry.mirror_perm(N, s)
+    P = amg.Problem(A.shape[0], A.indptr, A.indices, A.data, s, perm)
+    rp, ci, v = P.inner_block()
+    Ainn = sp.csr_matrix((v, ci, rp), shape=(P.n_b, P.n_b))
+    H = symmetry.blocks(A, perm)
+    assert (Ainn != H[0]).nnz == 0  # bit-exact extraction
+    r, c, iv = P.interface()
+    hat = transform.hat_blocks_sparse(H)
+    for i in range(1 << s):
+        Aout = sp.csr_matrix((iv[:, i], (r, c)), shape=Ainn.shape)
+        ref = hat[i] - H[0]
+        assert abs(Aout - ref).max() <= 1e-15 * abs(H[0]).max()
+
+
+def test_create_problem_rejects_bad_map():
+    g, A = _oracle_problem((8, 6), 1)
+    perm = symmetry.mirror_perm((8, 6), 1).copy()
+    perm[1, 0] = perm[0, 0]
+    with pytest.raises(amg.AmgsymError) as e:
+        amg.Problem(A.shape[0], A.indptr, A.indices, A.data, 1, perm)
+    assert e.value.name == "ERR_MAP"
+    perm = symmetry.mirror_perm((8, 6), 1).copy()
+    perm[0, 0] = 10**6
+    with pytest.raises(amg.AmgsymError) as e:
+        amg.Problem(A.shape[0], A.indptr, A.indices, A.data, 1, perm)
+    assert e.value.name == "ERR_MAP"
+
+
+def test_create_problem_rejects_asymmetric_coefficient():
+    N = (8, 6)
+    g = np.random.default_rng(1).standard_normal(48)  # breaks the mirror symmetry
+    h, k, A = fv.grid_operator(N, 0.0, g)
+    perm = symmetry.mirror_perm(N, 1)
+    with pytest.raises(amg.AmgsymError) as e:
+        amg.Problem(A.shape[0], A.indptr, A.indices, A.data, 1, perm)
+    assert e.value.name == "ERR_NOT_SYMMETRIC"
+
+
+def test_create_problem_rejects_nonsymmetric_matrix():
+    g, A = _oracle_problem((8, 6), 1)
+    A = A.tolil()
+    # perturb one pair of mirror entries consistently but not symmetrically
+    perm = symmetry.mirror_perm((8, 6), 1)
+    p0, q0 = perm[0, 0], perm[0, 1]
+    p1, q1 = perm[1, 0], perm[1, 1]
+    A[p0, q0] = A[p0, q0] * 1.5
+    A[p1, q1] = A[p1, q1] * 1.5
+    A = A.tocsr()
+    with pytest.raises(amg.AmgsymError) as e:
+        amg.Problem(A.shape[0], A.indptr, A.indices, A.data, 1, perm)
+    assert e.value.name == "ERR_NOT_SYMMETRIC"
+
+
+def test_create_problem_rejects_bad_csr():
+    g, A = _oracle_problem((8, 6), 1)
+    perm = symmetry.mirror_perm((8, 6), 1)
+    ci = A.indices.copy()
+    ci[3] = -1
+    with pytest.raises(amg.AmgsymError) as e:
+        amg.Problem(A.shape[0], A.indptr, ci, A.data, 1, perm)
+    assert e.value.name == "ERR_ARG"
+    with pytest.raises(amg.AmgsymError):
+        amg.Problem(A.shape[0], A.indptr, A.indices, A.data, 1, perm[:, :-1].copy().reshape(-1)[: A.shape[0] - 2])
+
+
+def _csr(t):
+    rp, ci, v, shape = t
+    return sp.csr_matrix((v, ci, rp), shape=shape)
+
+
+def test_hierarchy_structure():
+    N, s = (32, 32, 32), 3
+    g = gaussian_logk(N, s, seed=3, corr=4.0)
+    P = amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, coarse_max=128)
+    L = P.num_levels()
+    assert L >= 3
+    A0 = _csr(P.level_matrix(0, "A"))
+    rp, ci, v = P.inner_block()
+    assert (A0 != sp.csr_matrix((v, ci, rp), shape=A0.shape)).nnz == 0
+    for l in range(L - 1):
+        A = _csr(P.level_matrix(l, "A"))
+        Pm = _csr(P.level_matrix(l, "P"))
+        G = _csr(P.level_matrix(l, "G"))
+        Ac = _csr(P.level_matrix(l + 1, "A"))
+        # Galerkin coarse operator R A P with R = P^T
+        ref = (Pm.T @ A @ Pm).tocsr()
+        assert abs(Ac - ref).max() <= 1e-12 * abs(ref).max()
+        # C points interpolate by injection: some rows are unit vectors
+        assert np.isclose(Pm.max(), 1.0) or Pm.max() >= 1.0
+        # FSAI: lower triangular, G A G^T has unit diagonal
+        assert sp.triu(G, k=1).nnz == 0
+        d = (G @ A @ G.T).diagonal()
+        assert np.max(np.abs(d - 1.0)) < 1e-10
+        inf = P.level_info(l)
+        assert 0.0 < inf["omega"] < 2.0
+    assert P.level_info(L - 1)["rows"] <= 128
