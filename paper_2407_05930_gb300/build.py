@@ -4,7 +4,7 @@ Compiles the CUDA translation units and the host C++ (OpenMP) in parallel
 and links ``libamgsym.so`` next to this file.  Used by
 ``__graft_entry__.build()`` and importable on its own::
 
-    python -m paper_2407_05930_gb300.build
+    python paper_2407_05930_gb300/build.py
 """
 
 from __future__ import annotations
