@@ -261,6 +261,10 @@ amgsym_status amgsym_fv_grad_logk(int32_t d, const int64_t* N, const double* wid
                                   const double* lam_dev, int32_t nrhs, int64_t ld,
                                   double* grad_dev, int32_t accumulate, void* stream);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (a replayed CUDA graph counts its kernels).  Host-side counter. */
+int64_t amgsym_kernel_launches(void);
+
 void amgsym_destroy(amgsym_t h);
 
 #ifdef __cplusplus

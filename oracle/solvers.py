@@ -69,13 +69,16 @@ def cg(A, b: np.ndarray, tol: float = 1e-13, maxit: int = 200000, x0=None, retur
     return (x, info) if return_info else x
 
 
-def cg_iteration_time(A, b: np.ndarray, iters: int) -> float:
-    """Seconds per iteration of ``cg``'s loop body over ``iters`` iterations
-    (used to time the oracle on a bounded sample of a large workload)."""
+def cg_sample(A, b: np.ndarray, iters: int):
+    """Run ``iters`` iterations of ``cg``'s loop body from x = 0 and return
+    (seconds per iteration, alphas, betas).  Used to time the oracle on a
+    bounded sample of a large workload; the CG coefficients define the Lanczos
+    tridiagonal whose extreme Ritz values bound the spectrum from inside."""
     x = np.zeros_like(b)
     r = b.copy()
     p = r.copy()
     rr = float(r @ r)
+    alphas, betas = [], []
     t0 = time.perf_counter()
     for _ in range(iters):
         q = A @ p
@@ -83,10 +86,26 @@ def cg_iteration_time(A, b: np.ndarray, iters: int) -> float:
         x += alpha * p
         r -= alpha * q
         rr_new = float(r @ r)
-        p *= rr_new / rr
+        beta = rr_new / rr
+        p *= beta
         p += r
         rr = rr_new
-    return (time.perf_counter() - t0) / iters
+        alphas.append(alpha)
+        betas.append(beta)
+    return (time.perf_counter() - t0) / iters, alphas, betas
+
+
+def lanczos_condition_estimate(alphas, betas) -> float:
+    """``theta_max / theta_min`` of the CG-Lanczos tridiagonal (a lower bound
+    on the condition number of the matrix CG ran on)."""
+    k = len(alphas)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(betas[j]) / alphas[j]
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[-1] / ev[0])
 
 
 def _axis_weights(N):

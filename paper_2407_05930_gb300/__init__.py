@@ -120,6 +120,7 @@ def _load():
         "amgsym_fv_assemble": (i32, [i32, pi64, pdbl, pdbl, pi64, pi32, pdbl]),
         "amgsym_mirror_perm": (i32, [i32, pi64, i32, pi32]),
         "amgsym_fv_grad_logk": (i32, [i32, pi64, P, P, P, P, i32, i64, P, i32, P]),
+        "amgsym_kernel_launches": (i64, []),
         "amgsym_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -140,9 +141,14 @@ EXPORTED = [
         "amgsym_num_levels amgsym_level_sizes amgsym_get_level_matrix amgsym_solve "
         "amgsym_solve_adjoint amgsym_transform_forward amgsym_transform_backward "
         "amgsym_apply_reduced amgsym_vcycle amgsym_grid_widths amgsym_fv_nnz "
-        "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_destroy"
+        "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy"
     ).split()
 ]
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib.amgsym_kernel_launches())
 
 
 def _check(code: int):

@@ -143,6 +143,11 @@ void launch_fv_grad(int32_t d, const int64_t* N, const double* widths, const dou
                     const double* lam, int32_t nrhs, int64_t ld, double* grad, int32_t accumulate,
                     cudaStream_t st);
 
+// Host-side count of kernel launches issued by this library (graph replays
+// add the number of kernels in the graph).
+void count_launch(int64_t n = 1);
+int64_t launch_count();
+
 int num_sms();
 int max_grid_blocks();  // blocks for grid-stride kernels (SMs x resident blocks)
 

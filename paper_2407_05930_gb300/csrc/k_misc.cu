@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "device.h"
 #include "dot.cuh"
@@ -10,6 +11,10 @@
 namespace amgsym {
 
 static int g_sms = 0;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int num_sms() {
   if (g_sms == 0) {
@@ -109,6 +114,7 @@ static void fwd_dispatch(const double* b, int32_t nrhs, int64_t ld, const int32_
 
 void launch_transform_fwd(const double* b, int32_t nrhs, int64_t ld, const int32_t* perm, int64_t n_b, int32_t s,
                           void* xhat, VecType ot, cudaStream_t st) {
+  count_launch();
   if (ot == VEC_F64)
     fwd_dispatch<double>(b, nrhs, ld, perm, n_b, s, static_cast<double*>(xhat), st);
   else
@@ -131,6 +137,7 @@ static void bwd_dispatch(const IT* xhat, int32_t nrhs, const int32_t* perm, int6
 
 void launch_transform_bwd(const void* xhat, VecType it, int32_t nrhs, const int32_t* perm, int64_t n_b, int32_t s,
                           double* x, int64_t ld, cudaStream_t st) {
+  count_launch();
   if (it == VEC_F64)
     bwd_dispatch<double>(static_cast<const double*>(xhat), nrhs, perm, n_b, s, x, ld, st);
   else
@@ -200,6 +207,7 @@ static void update1_t(int64_t rows, int32_t C, void* x, void* r, const void* p, 
 
 void launch_cg_update1(VecType vt, int64_t rows, int32_t C, void* x, void* r, const void* p, const void* q,
                        const DotArgs& dot, cudaStream_t st) {
+  count_launch();
   if (vt == VEC_F64)
     update1_t<double>(rows, C, x, r, p, q, dot, st);
   else
@@ -217,6 +225,7 @@ __global__ void __launch_bounds__(kBlock) cg_update2_kernel(int64_t count, int32
 
 void launch_cg_update2(VecType vt, int64_t rows, int32_t C, void* p, const void* z, const double* beta,
                        cudaStream_t st) {
+  count_launch();
   const int64_t count = rows * C;
   const int g = grid_for(count, kBlock);
   if (vt == VEC_F64)
@@ -232,6 +241,7 @@ __global__ void add_to_f64_kernel(int64_t count, double* __restrict__ y, const T
 }
 
 void launch_add_to_f64(VecType xt, int64_t count, double* y, const void* x, cudaStream_t st) {
+  count_launch();
   const int g = grid_for(count, kBlock);
   if (xt == VEC_F64)
     add_to_f64_kernel<double><<<g, kBlock, 0, st>>>(count, y, static_cast<const double*>(x));
@@ -246,6 +256,7 @@ __global__ void copy_kernel(int64_t count, T* __restrict__ d, const T* __restric
 }
 
 void launch_copy(VecType vt, int64_t count, void* dst, const void* src, cudaStream_t st) {
+  count_launch();
   const int g = grid_for(count, kBlock);
   if (vt == VEC_F64)
     copy_kernel<double><<<g, kBlock, 0, st>>>(count, static_cast<double*>(dst), static_cast<const double*>(src));
@@ -260,6 +271,7 @@ __global__ void zero_kernel(int64_t count, T* __restrict__ d) {
 }
 
 void launch_zero(VecType vt, int64_t count, void* dst, cudaStream_t st) {
+  count_launch();
   const int g = grid_for(count, kBlock);
   if (vt == VEC_F64)
     zero_kernel<double><<<g, kBlock, 0, st>>>(count, static_cast<double*>(dst));
@@ -285,6 +297,7 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(int64_t rows, int32_t C, co
 
 void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,
                 cudaStream_t st) {
+  count_launch();
   int g = grid_for(rows, kBlock / C > 0 ? kBlock / C : 1);
   if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
   if (vt == VEC_F64)
@@ -316,6 +329,7 @@ __global__ void __launch_bounds__(kBlock) coarse_kernel(int32_t n, int32_t C, co
 
 void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
                          cudaStream_t st) {
+  count_launch();
   const int64_t total = (int64_t)n * C;
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 63) / 64, max_grid_blocks()));
   if (vt == VEC_F64)
@@ -349,6 +363,7 @@ __global__ void init_scalars_kernel(DevScalars sc, int32_t nrhs, int32_t nb) {
 }
 
 void launch_init_scalars(const DevScalars& sc, int32_t nrhs, int32_t nb, cudaStream_t st) {
+  count_launch();
   init_scalars_kernel<<<1, kBlock, 0, st>>>(sc, nrhs, nb);
 }
 
@@ -410,6 +425,7 @@ __global__ void __launch_bounds__(kBlock) fv_grad_kernel(GridDev g, const double
 void launch_fv_grad(int32_t d, const int64_t* N, const double* widths, const double* k, const double* u,
                     const double* lam, int32_t nrhs, int64_t ld, double* grad, int32_t accumulate,
                     cudaStream_t st) {
+  count_launch();
   GridDev g;
   g.d = d;
   int64_t off = 0;

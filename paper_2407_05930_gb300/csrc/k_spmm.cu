@@ -207,6 +207,7 @@ static void launch_t(const SpmmArgs& a, cudaStream_t st) {
   if (grid < 1) grid = 1;
   const bool dot = a.dot.mode != DOT_NONE;
   const bool ifc = a.imask != nullptr;
+  count_launch();
   if (dot) {
     if ((int64_t)grid * a.C > a.dot.sc.partial_cap) grid = (int)(a.dot.sc.partial_cap / a.C);
     if (ifc)

@@ -80,6 +80,7 @@ struct Device {
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   GraphCache graph;
+  int64_t graph_kernels = 0;
 };
 
 template <typename T>
@@ -416,6 +417,7 @@ static int pcg_loop(const Ctx& c, PrecWork& W, const DevScalars& sc, int32_t nrh
       Ctx cc = c;
       cc.st = D->cap_stream;
       cudaGraph_t g = nullptr;
+      const int64_t before = launch_count();
       CK(cudaStreamBeginCapture(D->cap_stream, cudaStreamCaptureModeThreadLocal));
       try {
         pcg_iteration(cc, W, sc, nrhs, tol);
@@ -426,6 +428,8 @@ static int pcg_loop(const Ctx& c, PrecWork& W, const DevScalars& sc, int32_t nrh
         throw;
       }
       CK(cudaStreamEndCapture(D->cap_stream, &g));
+      D->graph_kernels = launch_count() - before;
+      count_launch(-D->graph_kernels);  // captured, not executed
       CK(cudaGraphInstantiate(&exec, g, 0));
       cudaGraphDestroy(g);
       D->graph.exec = exec;
@@ -442,6 +446,7 @@ static int pcg_loop(const Ctx& c, PrecWork& W, const DevScalars& sc, int32_t nrh
   for (it = 0; it < maxit; ++it) {
     if (exec) {
       CK(cudaGraphLaunch(exec, c.st));
+      count_launch(D->graph_kernels);
       CK(cudaEventRecord(D->ev[0], c.st));
       CK(cudaEventSynchronize(D->ev[0]));
       std::memcpy(st4, D->h_status, sizeof(st4));
@@ -691,3 +696,5 @@ extern "C" amgsym_status amgsym_fv_grad_logk(int32_t d, const int64_t* N, const 
   check_launch();
   API_END
 }
+
+extern "C" int64_t amgsym_kernel_launches(void) { return amgsym::launch_count(); }

@@ -93,3 +93,16 @@ def test_adjoint_fd_32cube():
     eps = 1e-6
     fd = (adjoint.loss(h, g + eps * v, b, ut) - adjoint.loss(h, g - eps * v, b, ut)) / (2 * eps)
     assert abs(fd - dLdg @ v) <= 1e-6 * abs(fd)
+
+
+def test_lanczos_condition_estimate_bounds_true_condition():
+    # the CG-Lanczos Ritz values lie inside the spectrum; for a small matrix
+    # and enough iterations they converge to the extremes
+    h, k, A = fv.grid_operator((12, 10), 0.0)
+    ev = np.linalg.eigvalsh(A.toarray())
+    b = rhs_uniform(A.shape[0], 1, config=97)[0]
+    t, al, be = solvers.cg_sample(A, b, 40)
+    kap = solvers.lanczos_condition_estimate(al, be)
+    true = ev[-1] / ev[0]
+    assert kap <= true * (1 + 1e-8)
+    assert kap >= 0.9 * true
