@@ -264,10 +264,15 @@ def run_gpu(args):
             sec = float(t.item())
         return sec, amg.kernel_launches() - l0
 
+    nvtx = torch.cuda.nvtx
     with ClockSampler(torch.cuda.current_device()) as clk:
+        nvtx.range_push("timed_mixed")
         sec_m, launches_m = timed(mixed, args.steps)
+        nvtx.range_pop()
     clocks = clk.summary()
+    nvtx.range_push("timed_fp64")
     sec_d, launches_d = timed(fp64, max(1, args.steps // 2))
+    nvtx.range_pop()
     steps_d = max(1, args.steps // 2)
 
     # end to end through the public API: pinned host b -> device -> solve -> host x
@@ -296,7 +301,9 @@ def run_gpu(args):
     _, info_m = P.solve(b, x, **mixed)
     _, info_d = P.solve(b, x, **fp64)
 
+    nvtx.range_push("roofline")
     t_k, algo = _spmm_roofline(P, amg, torch, nrhs)
+    nvtx.range_pop()
     peak, peak_kind = _peaks()
     achieved = algo / t_k / 1e9
 
