@@ -60,6 +60,7 @@ struct DevScalars {
   double* rr = nullptr;      // <r, r> per column (last computed)
   double* bnorm2 = nullptr;  // ||b^||^2 per RHS (reference for the stopping test)
   double* relres = nullptr;  // per RHS
+  double* tol2 = nullptr;    // squared relative-residual target (device scalar)
   int32_t* active = nullptr; // per column: 1 while its RHS has not converged
   int32_t* status = nullptr; // [0] active RHS count, [1] breakdown flag, [2] iterations
   double* partials = nullptr;  // dot-product block partials
@@ -67,9 +68,9 @@ struct DevScalars {
   int64_t partial_cap = 0;     // doubles available in partials
 };
 
-// Tolerance block for the convergence finalisation.
+// Shape block for the convergence finalisation (the tolerance itself is the
+// device scalar DevScalars::tol2, so captured graphs do not depend on it).
 struct ConvParams {
-  double tol2;       // tol^2
   int32_t nrhs, nb;  // columns = nrhs * nb
   int32_t count_iter;
 };
@@ -110,6 +111,9 @@ struct SpmmArgs {
   const int32_t* icol = nullptr;
   const void* ival = nullptr;  // same precision class as the accumulation
   int32_t nb = 1;
+  // Early exit: when non-NULL and *skip == 0 (no active RHS) the kernel does
+  // nothing (lets the host run one iteration ahead of its convergence check).
+  const int32_t* skip = nullptr;
   DotArgs dot;
 };
 
@@ -123,20 +127,22 @@ void launch_transform_bwd(const void* xhat, VecType it, int32_t nrhs, const int3
                           int32_t s, double* x, int64_t ld, cudaStream_t st);
 // x += alpha p ; r -= alpha q ; rr = <r, r>  (finalisation FIN_CONV)
 void launch_cg_update1(VecType vt, int64_t rows, int32_t C, void* x, void* r, const void* p,
-                       const void* q, const DotArgs& dot, cudaStream_t st);
+                       const void* q, const DotArgs& dot, cudaStream_t st, const int32_t* skip = nullptr);
 // p = z + beta p
 void launch_cg_update2(VecType vt, int64_t rows, int32_t C, void* p, const void* z,
-                       const double* beta, cudaStream_t st);
+                       const double* beta, cudaStream_t st, const int32_t* skip = nullptr);
 // y (f64) += x (f32 or f64)
 void launch_add_to_f64(VecType xt, int64_t count, double* y, const void* x, cudaStream_t st);
 void launch_copy(VecType vt, int64_t count, void* dst, const void* src, cudaStream_t st);
 void launch_zero(VecType vt, int64_t count, void* dst, cudaStream_t st);
 // dot over a whole [rows][C] array (for ||b^||^2 etc.)
 void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,
-                cudaStream_t st);
+                cudaStream_t st, const int32_t* skip = nullptr);
 // Z = Ainv Y (dense coarsest solve, FP64 arithmetic)
 void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
-                         cudaStream_t st);
+                         cudaStream_t st, const int32_t* skip = nullptr);
+// *dst = v (a one-thread kernel, so the write is ordered on the stream and capturable)
+void launch_set_value(double* dst, double v, cudaStream_t st);
 // CG initial scalars: active = 1 for columns of RHS with nonzero ||b||, status reset.
 void launch_init_scalars(const DevScalars& sc, int32_t nrhs, int32_t nb, cudaStream_t st);
 void launch_fv_grad(int32_t d, const int64_t* N, const double* widths, const double* k, const double* u,

@@ -68,7 +68,7 @@ __device__ __forceinline__ void dot_finalize_rhs(const DotArgs& d, const double*
     const double rel2 = bn > 0.0 ? t / bn : 0.0;
     s.relres[r] = sqrt(rel2);
     bool act = s.active[r * nb] != 0;
-    if (act && !(rel2 > d.cp.tol2)) {  // converged (NaN keeps it active)
+    if (act && !(rel2 > *s.tol2)) {  // converged (NaN keeps it active)
       act = false;
       for (int i = 0; i < nb; ++i) s.active[r * nb + i] = 0;
     }

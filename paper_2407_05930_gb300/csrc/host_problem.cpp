@@ -66,7 +66,7 @@ extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {
   o->maxit = 500;
   o->precision = AMGSYM_PREC_FP64;
   o->use_x0 = 0;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-5;
   o->max_outer = 20;
   o->finest_hat = 0;
   o->use_graph = 1;

@@ -161,8 +161,10 @@ struct DotAcc<double> {
 template <typename T, int CPT, bool HAS_DOT>
 __global__ void __launch_bounds__(kBlock) cg_update1_kernel(int64_t rows, int32_t C, T* __restrict__ x,
                                                             T* __restrict__ r, const T* __restrict__ p,
-                                                            const T* __restrict__ q, DotArgs dot) {
+                                                            const T* __restrict__ q, DotArgs dot,
+                                                            const int32_t* skip) {
   using DT = typename DotAcc<T>::type;
+  if (skip && *skip == 0) return;
   const int TPR = C / CPT;
   const int rows_pb = kBlock / TPR;
   const int rloc = threadIdx.x / TPR;
@@ -198,25 +200,27 @@ __global__ void __launch_bounds__(kBlock) cg_update1_kernel(int64_t rows, int32_
 
 template <typename T>
 static void update1_t(int64_t rows, int32_t C, void* x, void* r, const void* p, const void* q, const DotArgs& dot,
-                      cudaStream_t st) {
+                      cudaStream_t st, const int32_t* skip) {
   int g = grid_for(rows, kBlock / C > 0 ? kBlock / C : 1);
   if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
   cg_update1_kernel<T, 1, true><<<g, kBlock, 0, st>>>(rows, C, static_cast<T*>(x), static_cast<T*>(r),
-                                                      static_cast<const T*>(p), static_cast<const T*>(q), dot);
+                                                      static_cast<const T*>(p), static_cast<const T*>(q), dot, skip);
 }
 
 void launch_cg_update1(VecType vt, int64_t rows, int32_t C, void* x, void* r, const void* p, const void* q,
-                       const DotArgs& dot, cudaStream_t st) {
+                       const DotArgs& dot, cudaStream_t st, const int32_t* skip) {
   count_launch();
   if (vt == VEC_F64)
-    update1_t<double>(rows, C, x, r, p, q, dot, st);
+    update1_t<double>(rows, C, x, r, p, q, dot, st, skip);
   else
-    update1_t<float>(rows, C, x, r, p, q, dot, st);
+    update1_t<float>(rows, C, x, r, p, q, dot, st, skip);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) cg_update2_kernel(int64_t count, int32_t C, T* __restrict__ p,
-                                                            const T* __restrict__ z, const double* __restrict__ beta) {
+                                                            const T* __restrict__ z, const double* __restrict__ beta,
+                                                            const int32_t* skip) {
+  if (skip && *skip == 0) return;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
     const T b = (T)beta[e % C];
     p[e] = z[e] + b * p[e];
@@ -224,14 +228,14 @@ __global__ void __launch_bounds__(kBlock) cg_update2_kernel(int64_t count, int32
 }
 
 void launch_cg_update2(VecType vt, int64_t rows, int32_t C, void* p, const void* z, const double* beta,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int32_t* skip) {
   count_launch();
   const int64_t count = rows * C;
   const int g = grid_for(count, kBlock);
   if (vt == VEC_F64)
-    cg_update2_kernel<double><<<g, kBlock, 0, st>>>(count, C, static_cast<double*>(p), static_cast<const double*>(z), beta);
+    cg_update2_kernel<double><<<g, kBlock, 0, st>>>(count, C, static_cast<double*>(p), static_cast<const double*>(z), beta, skip);
   else
-    cg_update2_kernel<float><<<g, kBlock, 0, st>>>(count, C, static_cast<float*>(p), static_cast<const float*>(z), beta);
+    cg_update2_kernel<float><<<g, kBlock, 0, st>>>(count, C, static_cast<float*>(p), static_cast<const float*>(z), beta, skip);
 }
 
 template <typename T>
@@ -281,7 +285,8 @@ void launch_zero(VecType vt, int64_t count, void* dst, cudaStream_t st) {
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) dot_kernel(int64_t rows, int32_t C, const T* __restrict__ a,
-                                                     const T* __restrict__ b, DotArgs dot) {
+                                                     const T* __restrict__ b, DotArgs dot, const int32_t* skip) {
+  if (skip && *skip == 0) return;
   const int TPR = C;
   const int rows_pb = kBlock / TPR;
   const int rloc = threadIdx.x / TPR;
@@ -296,14 +301,14 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(int64_t rows, int32_t C, co
 }
 
 void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,
-                cudaStream_t st) {
+                cudaStream_t st, const int32_t* skip) {
   count_launch();
   int g = grid_for(rows, kBlock / C > 0 ? kBlock / C : 1);
   if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
   if (vt == VEC_F64)
-    dot_kernel<double><<<g, kBlock, 0, st>>>(rows, C, static_cast<const double*>(a), static_cast<const double*>(b), dot);
+    dot_kernel<double><<<g, kBlock, 0, st>>>(rows, C, static_cast<const double*>(a), static_cast<const double*>(b), dot, skip);
   else
-    dot_kernel<float><<<g, kBlock, 0, st>>>(rows, C, static_cast<const float*>(a), static_cast<const float*>(b), dot);
+    dot_kernel<float><<<g, kBlock, 0, st>>>(rows, C, static_cast<const float*>(a), static_cast<const float*>(b), dot, skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,7 +316,9 @@ void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* 
 // Z = A_c^{-1} Y with the precomputed FP64 inverse; FP64 arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) coarse_kernel(int32_t n, int32_t C, const double* __restrict__ Ainv,
-                                                        const T* __restrict__ Y, T* __restrict__ Z) {
+                                                        const T* __restrict__ Y, T* __restrict__ Z,
+                                                        const int32_t* skip) {
+  if (skip && *skip == 0) return;
   const int64_t total = (int64_t)n * C;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / C, c = t - i * C;
@@ -328,14 +335,21 @@ __global__ void __launch_bounds__(kBlock) coarse_kernel(int32_t n, int32_t C, co
 }
 
 void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
-                         cudaStream_t st) {
+                         cudaStream_t st, const int32_t* skip) {
   count_launch();
   const int64_t total = (int64_t)n * C;
   const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 63) / 64, max_grid_blocks()));
   if (vt == VEC_F64)
-    coarse_kernel<double><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const double*>(Y), static_cast<double*>(Z));
+    coarse_kernel<double><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const double*>(Y), static_cast<double*>(Z), skip);
   else
-    coarse_kernel<float><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const float*>(Y), static_cast<float*>(Z));
+    coarse_kernel<float><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const float*>(Y), static_cast<float*>(Z), skip);
+}
+
+__global__ void set_value_kernel(double* dst, double v) { *dst = v; }
+
+void launch_set_value(double* dst, double v, cudaStream_t st) {
+  count_launch();
+  set_value_kernel<<<1, 1, 0, st>>>(dst, v);
 }
 
 __global__ void init_scalars_kernel(DevScalars sc, int32_t nrhs, int32_t nb) {

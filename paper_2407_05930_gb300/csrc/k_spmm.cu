@@ -98,6 +98,7 @@ template <typename MT, typename XT, typename OT, int CPT, bool HAS_DOT, bool HAS
 __global__ void __launch_bounds__(kBlock) spmm_kernel(SpmmArgs a) {
   using CT = typename ComputeOf<MT, XT>::type;
   using DT = typename AccOf<XT>::type;  // per-thread dot partial type
+  if (a.skip && *a.skip == 0) return;  // uniform over the grid
   const int C = a.C;
   const int TPR = C / CPT;
   const int rows_pb = kBlock / TPR;

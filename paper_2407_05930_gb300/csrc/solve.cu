@@ -222,6 +222,7 @@ static void alloc_scalars(Device* D, DevScalars& sc, int32_t C, int32_t nrhs) {
   sc.rr = dalloc<double>(D->work_owned, C);
   sc.bnorm2 = dalloc<double>(D->work_owned, nrhs);
   sc.relres = dalloc<double>(D->work_owned, nrhs);
+  sc.tol2 = dalloc<double>(D->work_owned, 1);
   sc.active = dalloc<int32_t>(D->work_owned, C);
   sc.status = dalloc<int32_t>(D->work_owned, 4);
   sc.partial_cap = (int64_t)max_grid_blocks() * C;
@@ -284,6 +285,7 @@ struct Ctx {
   ValType mt;       // matrix value precision of the V-cycle
   bool finest_hat;  // V-cycle level-0 residual with A^_i
   cudaStream_t st;
+  const int32_t* skip = nullptr;  // early-exit flag (active RHS count) of the PCG loop
 };
 
 static void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X, void* Y,
@@ -310,6 +312,7 @@ static void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType 
     a.nb = c.D->nb;
   }
   if (dot) a.dot = *dot;
+  a.skip = c.skip;
   launch_spmm(mt, xt, ot, a, c.st);
   check_launch();
 }
@@ -323,10 +326,10 @@ static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* l
   PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
   LevelWork& lw = W.lw[l];
   if (L.cinv) {
-    launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st);
+    launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st, c.skip);
     check_launch();
     if (last) {
-      launch_dot(c.vt, L.n, c.C, last->W, z, *last, c.st);
+      launch_dot(c.vt, L.n, c.C, last->W, z, *last, c.st, c.skip);
       check_launch();
     }
     return;
@@ -358,13 +361,12 @@ static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* l
 }
 
 static DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb,
-                        double tol, int count_iter) {
+                        double /*tol: the device scalar sc.tol2 holds it*/, int count_iter) {
   DotArgs d;
   d.mode = mode;
   d.final = final;
   d.W = W;
   d.sc = sc;
-  d.cp.tol2 = tol * tol;
   d.cp.nrhs = nrhs;
   d.cp.nb = nb;
   d.cp.count_iter = count_iter;
@@ -379,11 +381,11 @@ static void pcg_iteration(const Ctx& c, PrecWork& W, const DevScalars& sc, int32
   DotArgs dpq = make_dot(sc, DOT_WY, FIN_ALPHA, W.p, nrhs, D->nb, tol, 0);
   spmm(c, D->Ainn, kmt, c.vt, c.vt, W.p, W.q, 1.0, 0.0, nullptr, true, &dpq);
   DotArgs drr = make_dot(sc, DOT_YY, FIN_CONV, nullptr, nrhs, D->nb, tol, 1);
-  launch_cg_update1(c.vt, D->n_b, c.C, W.x, W.r, W.p, W.q, drr, c.st);
+  launch_cg_update1(c.vt, D->n_b, c.C, W.x, W.r, W.p, W.q, drr, c.st, c.skip);
   check_launch();
   DotArgs drz = make_dot(sc, DOT_WY, FIN_BETA, W.r, nrhs, D->nb, tol, 0);
   vcycle(c, 0, W.r, W.z, &drz);
-  launch_cg_update2(c.vt, D->n_b, c.C, W.p, W.z, sc.beta, c.st);
+  launch_cg_update2(c.vt, D->n_b, c.C, W.p, W.z, sc.beta, c.st, c.skip);
   check_launch();
 }
 
@@ -394,14 +396,18 @@ static void read_status(Device* D, const DevScalars& sc, cudaStream_t st, int32_
 }
 
 // PCG loop until every RHS of `sc` is inactive or maxit; returns iterations.
-// The host checks the status of iteration k while iteration k + 1 runs.
-static int pcg_loop(const Ctx& c, PrecWork& W, const DevScalars& sc, int32_t nrhs, double tol, int maxit,
+// The host runs one iteration ahead: it enqueues iteration k + 1 before
+// waiting for the status of iteration k.  Kernels of an iteration that starts
+// after convergence exit at once (Ctx::skip), so the look-ahead costs only
+// launch latency and the GPU never idles on the host's check.
+static int pcg_loop(const Ctx& c0, PrecWork& W, const DevScalars& sc, int32_t nrhs, double tol, int maxit,
                     bool use_graph, int graph_mode, bool* breakdown) {
+  Device* D = c0.D;
+  Ctx c = c0;
+  c.skip = sc.status;
   GraphKey graph_key;
   graph_key.mode = graph_mode;
   graph_key.nrhs = nrhs;
-  graph_key.tol = tol;
-  Device* D = c.D;
   // start: z = M r, rz, p = z
   DotArgs drz = make_dot(sc, DOT_WY, FIN_STORE_RZ, W.r, nrhs, D->nb, tol, 0);
   vcycle(c, 0, W.r, W.z, &drz);
@@ -421,7 +427,6 @@ static int pcg_loop(const Ctx& c, PrecWork& W, const DevScalars& sc, int32_t nrh
       CK(cudaStreamBeginCapture(D->cap_stream, cudaStreamCaptureModeThreadLocal));
       try {
         pcg_iteration(cc, W, sc, nrhs, tol);
-        CK(cudaMemcpyAsync(D->h_status, sc.status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, D->cap_stream));
       } catch (...) {
         cudaStreamEndCapture(D->cap_stream, &g);
         if (g) cudaGraphDestroy(g);
@@ -436,34 +441,35 @@ static int pcg_loop(const Ctx& c, PrecWork& W, const DevScalars& sc, int32_t nrh
       D->graph.key = graph_key;
     }
   }
-  // Two status slots so the copy of iteration k is not overwritten by k+1
-  // before the host reads it: slot = k % 2 (graph path writes slot 0 only,
-  // so it synchronises per iteration via the event).
-  int it = 0;
-  int done_at = -1;
   *breakdown = false;
-  int32_t st4[4];
+  int done_at = -1;
+  auto check = [&](int k) -> bool {  // status after iteration k (0-based)
+    CK(cudaEventSynchronize(D->ev[k & 1]));
+    const int32_t* st4 = D->h_status + 4 * (k & 1);
+    if (st4[1]) *breakdown = true;
+    if (st4[1] || st4[0] == 0) {
+      done_at = k + 1;
+      return true;
+    }
+    return false;
+  };
+  int it = 0;
   for (it = 0; it < maxit; ++it) {
     if (exec) {
       CK(cudaGraphLaunch(exec, c.st));
       count_launch(D->graph_kernels);
-      CK(cudaEventRecord(D->ev[0], c.st));
-      CK(cudaEventSynchronize(D->ev[0]));
-      std::memcpy(st4, D->h_status, sizeof(st4));
     } else {
       pcg_iteration(c, W, sc, nrhs, tol);
-      read_status(D, sc, c.st, st4);
     }
-    if (st4[1]) {
-      *breakdown = true;
-      done_at = it + 1;
-      break;
-    }
-    if (st4[0] == 0) {
-      done_at = it + 1;
-      break;
-    }
+    CK(cudaMemcpyAsync(D->h_status + 4 * (it & 1), sc.status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaEventRecord(D->ev[it & 1], c.st));
+    if (it >= 1 && check(it - 1)) break;
   }
+  if (done_at < 0 && it > 0) {
+    // maxit reached: the last iteration's status decides
+    if (!check(it - 1)) done_at = maxit;
+  }
+  CK(cudaStreamSynchronize(c.st));
   return done_at < 0 ? maxit : done_at;
 }
 
@@ -511,6 +517,8 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
   check_launch();
   launch_init_scalars(D->sc_out, nrhs, D->nb, st);
   check_launch();
+  launch_set_value(D->sc_out.tol2, o.tol * o.tol, st);
+  check_launch();
   if (o.use_x0) {
     launch_transform_fwd(x_dev, nrhs, ld, D->perm, D->n_b, D->s, D->xh, VEC_F64, st);
   } else {
@@ -551,6 +559,16 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
       spmm(c64, D->Ainn, VAL_F64, VEC_F64, VEC_F32, D->xh, W.r, -1.0, 1.0, D->bh, true, &drr);
       read_status(D, D->sc_out, st, st4);
       if (st4[0] == 0 || outer == o.max_outer || total_it >= o.maxit) break;
+      // Inner target: only as much reduction as the remaining distance to tol
+      // needs (with a 4x margin), but at least inner_tol, at most 0.5.
+      CK(cudaMemcpyAsync(D->h_relres, D->sc_out.relres, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      double worst = 0.0;
+      for (int r = 0; r < nrhs; ++r) worst = std::max(worst, D->h_relres[r]);
+      double eta = worst > 0.0 ? 0.25 * o.tol / worst : o.inner_tol;
+      eta = std::min(0.5, std::max(o.inner_tol, eta));
+      launch_set_value(D->sc_in.tol2, eta * eta, st);
+      check_launch();
       // inner reference norms ||r||^2 per RHS; inner active = outer active
       DotArgs dbi = make_dot(D->sc_in, DOT_WY, FIN_STORE_BN, nullptr, nrhs, D->nb, o.inner_tol, 0);
       launch_dot(VEC_F32, D->n_b, C, W.r, W.r, dbi, st);
