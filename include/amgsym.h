@@ -225,6 +225,29 @@ amgsym_status amgsym_apply_reduced(amgsym_t h, const void* X_dev, void* Y_dev, i
 amgsym_status amgsym_vcycle(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs,
                             int32_t prec, int32_t finest_hat, void* stream);
 
+/* Preconditioner without allocation: the V-cycle of amgsym_vcycle (same
+ * arguments, same kernels, same result), for callers that cannot let the
+ * library call cudaMalloc -- e.g. a real-time loop that must not take the
+ * device-wide synchronisation an allocation implies, or a process whose device
+ * memory belongs to another allocator with a fixed budget.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ *
+ * The level vectors come from one fixed array of 32 MiB (33554432 bytes) in
+ * device global memory, declared statically in the library; every GPU that
+ * loads the library holds it until the process exits.  A problem whose
+ * V-cycle needs more (sum over levels of 2 or 4 vectors of n_l x nrhs*2^s
+ * values, 8 bytes each in FP64 and 4 in the mixed modes, each rounded up to
+ * 256 bytes) is rejected with AMGSYM_ERR_ARG and a message giving both sizes.
+ * The entry point calls no cudaMalloc, cudaFree or other allocating routine.
+ * Its first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  All calls on a device share the one array and it
+ * keeps the last call's contents (every vector is written before it is read,
+ * so nothing needs clearing): calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. */
+amgsym_status amgsym_vcycle_noalloc(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs,
+                                    int32_t prec, int32_t finest_hat, void* stream);
+
 /* ------------------------------------------------------------------------
  * Structured-grid problem generator (host): the unit cube with N[a] cells
  * per axis (d = 1..3), cell-centred finite volumes for -div(k grad u) = f,

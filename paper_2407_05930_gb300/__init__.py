@@ -115,6 +115,7 @@ def _load():
         "amgsym_transform_backward": (i32, [P, P, i32, P, i64, P]),
         "amgsym_apply_reduced": (i32, [P, P, P, i32, i32, P]),
         "amgsym_vcycle": (i32, [P, P, P, i32, i32, i32, P]),
+        "amgsym_vcycle_noalloc": (i32, [P, P, P, i32, i32, i32, P]),
         "amgsym_grid_widths": (i32, [i64, dbl, pdbl]),
         "amgsym_fv_nnz": (i64, [i32, pi64]),
         "amgsym_fv_assemble": (i32, [i32, pi64, pdbl, pdbl, pi64, pi32, pdbl]),
@@ -140,7 +141,7 @@ EXPORTED = [
         "amgsym_problem_sizes amgsym_get_inner_block amgsym_get_interface amgsym_setup "
         "amgsym_num_levels amgsym_level_sizes amgsym_get_level_matrix amgsym_solve "
         "amgsym_solve_adjoint amgsym_transform_forward amgsym_transform_backward "
-        "amgsym_apply_reduced amgsym_vcycle amgsym_grid_widths amgsym_fv_nnz "
+        "amgsym_apply_reduced amgsym_vcycle amgsym_vcycle_noalloc amgsym_grid_widths amgsym_fv_nnz "
         "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy"
     ).split()
 ]
@@ -379,6 +380,13 @@ class Problem:
         _check(lib.amgsym_apply_reduced(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
                                         nrhs, prec, self._stream()))
         return Y
+
+    def vcycle_noalloc(self, R, Z, nrhs: int, prec: int = PREC_FP64, finest_hat: bool = False):
+        """The V-cycle with its work vectors in the library's fixed device
+        scratch (no allocation); see amgsym_vcycle_noalloc in include/amgsym.h."""
+        _check(lib.amgsym_vcycle_noalloc(self._h, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()),
+                                         nrhs, prec, 1 if finest_hat else 0, self._stream()))
+        return Z
 
     def vcycle(self, R, Z, nrhs: int, prec: int = PREC_FP64, finest_hat: bool = False):
         _check(lib.amgsym_vcycle(self._h, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()), nrhs, prec,

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -716,3 +717,128 @@ extern "C" amgsym_status amgsym_fv_grad_logk(int32_t d, const int64_t* N, const 
 }
 
 extern "C" int64_t amgsym_kernel_launches(void) { return amgsym::launch_count(); }
+
+// ---------------------------------------------------------------------------
+// V-cycle without allocation.
+//
+// amgsym_vcycle obtains its level work vectors from cudaMalloc on first use.
+// Some callers cannot allow that: a real-time loop that must not take the
+// device-wide synchronisation cudaMalloc/cudaFree imply, or a process whose
+// device memory is entirely owned by another allocator (a framework's caching
+// pool with a fixed budget), where a library-side cudaMalloc may fail or
+// fragment the pool.  amgsym_vcycle_noalloc runs the same V-cycle with its
+// level vectors carved from one fixed array in device global memory that the
+// library declares statically; it calls no allocating routine.
+
+namespace {
+
+// Fixed scratch shared by every call on a device.  It exists on every GPU
+// that loads this library, for the life of the process.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch for the current device.  In host code
+// the symbol name is only a host-side handle, so the address is looked up
+// once per device (with that device current) and cached.
+void* noalloc_scratch(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) fail(AMGSYM_ERR_ARG, "device ordinal out of range for the no-allocation path");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (!p) fail(AMGSYM_ERR_CUDA, "cudaGetSymbolAddress returned NULL for the no-allocation scratch");
+    g_noalloc_addr[dev] = p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+// The V-cycle of vcycle() above with caller-provided level buffers.
+void vcycle_with(const Ctx& c, std::vector<LevelWork>& lws, int l, const void* y, void* z) {
+  Device* D = c.D;
+  const DevLevel& L = D->lv[l];
+  LevelWork& lw = lws[l];
+  if (L.cinv) {
+    launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st, c.skip);
+    check_launch();
+    return;
+  }
+  const bool hat = c.finest_hat && l == 0;
+  const ValType mt = c.mt;
+  const VecType vt = c.vt;
+  spmm(c, L.G, mt, vt, vt, y, lw.t, 1.0, 0.0, nullptr, false, nullptr);
+  spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 0.0, nullptr, false, nullptr);
+  for (int k = 1; k < D->nu; ++k) {
+    spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+    spmm(c, L.G, mt, vt, vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 1.0, z, false, nullptr);
+  }
+  spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+  LevelWork& cw = lws[l + 1];
+  spmm(c, L.R, mt, vt, vt, lw.r, cw.y, 1.0, 0.0, nullptr, false, nullptr);
+  vcycle_with(c, lws, l + 1, cw.y, cw.z);
+  spmm(c, L.P, mt, vt, vt, cw.z, z, 1.0, 1.0, z, false, nullptr);
+  for (int k = 0; k < D->nu; ++k) {
+    spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+    spmm(c, L.G, mt, vt, vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 1.0, z, false, nullptr);
+  }
+}
+
+}  // namespace
+
+extern "C" amgsym_status amgsym_vcycle_noalloc(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs,
+                                               int32_t prec, int32_t finest_hat, void* stream) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (nrhs < 1 || (int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
+  check_ptr(R_dev, "R");
+  check_ptr(Z_dev, "Z");
+  if (R_dev == Z_dev) fail(AMGSYM_ERR_ARG, "R and Z must not overlap");
+  const bool f64 = prec == AMGSYM_PREC_FP64;
+  const VecType vt = f64 ? VEC_F64 : VEC_F32;
+  const ValType mt = f64 ? VAL_F64 : prec == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : VAL_F32;
+  const int32_t C = nrhs * D->nb;
+  const size_t es = f64 ? 8 : 4;
+  // Carve the level vectors (r, t on every level; y, z below the finest)
+  // from the fixed scratch, each 256-byte aligned.
+  std::vector<size_t> off;
+  size_t need = 0;
+  auto take = [&](int64_t rows) {
+    off.push_back(need);
+    need += ((size_t)rows * (size_t)C * es + 255) & ~size_t(255);
+  };
+  for (size_t l = 0; l < D->lv.size(); ++l) {
+    const int64_t n = D->lv[l].n;
+    take(n);  // r
+    take(n);  // t
+    if (l > 0) {
+      take(n);  // y
+      take(n);  // z
+    }
+  }
+  if (need > kNoAllocScratchBytes)
+    fail(AMGSYM_ERR_ARG, "amgsym_vcycle_noalloc: this problem needs " + std::to_string(need) +
+                             " bytes of V-cycle scratch for nrhs = " + std::to_string(nrhs) +
+                             "; the fixed scratch holds " + std::to_string(kNoAllocScratchBytes) +
+                             " bytes (use amgsym_vcycle)");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(dev));
+  std::vector<LevelWork> lws(D->lv.size());
+  size_t k = 0;
+  for (size_t l = 0; l < D->lv.size(); ++l) {
+    lws[l].r = base + off[k++];
+    lws[l].t = base + off[k++];
+    if (l > 0) {
+      lws[l].y = base + off[k++];
+      lws[l].z = base + off[k++];
+    }
+  }
+  Ctx c{D, C, vt, mt, finest_hat != 0, (cudaStream_t)stream};
+  vcycle_with(c, lws, 0, R_dev, Z_dev);
+  API_END
+}
