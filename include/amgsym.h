@@ -91,6 +91,9 @@ typedef struct {
   int32_t host_only;        /* 1: build the hierarchy on the host only, no
                                device upload (hierarchy export / CPU tests) */
   uint64_t seed;            /* PMIS random tie-breaking, default 12345 */
+  double coarse_drop;       /* sparsified Galerkin operators below the finest level:
+                               drop a_ij with |a_ij| < coarse_drop sqrt(a_ii a_jj),
+                               adding it to a_ii (0 = exact Galerkin), default 0 */
 } amgsym_opts;
 
 typedef struct {
@@ -104,6 +107,9 @@ typedef struct {
   int32_t max_outer;   /* mixed: refinement steps, 20 */
   int32_t finest_hat;  /* 1: V-cycle finest-level residuals use A^_i instead of A_inn */
   int32_t use_graph;   /* 1: capture one PCG iteration in a CUDA graph and replay it */
+  int32_t tune;        /* 1: time the SpMM tile candidates of every matrix once per
+                          column count and precision before the first PCG loop
+                          (default); 0: fixed tiles from the row lengths */
 } amgsym_solve_opts;
 
 typedef struct {

@@ -60,6 +60,7 @@ class Opts(ctypes.Structure):
         ("precisions", ctypes.c_int32),
         ("host_only", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
+        ("coarse_drop", ctypes.c_double),
     ]
 
 
@@ -73,6 +74,7 @@ class SolveOpts(ctypes.Structure):
         ("max_outer", ctypes.c_int32),
         ("finest_hat", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
+        ("tune", ctypes.c_int32),
     ]
 
 

@@ -21,6 +21,7 @@ enum VecType { VEC_F64 = 0, VEC_F32 = 1 };
 struct DevCsr {
   int32_t rows = 0, cols = 0;
   int64_t nnz = 0;
+  double avg_row = 0.0;  // nnz / rows (tile heuristic)
   int32_t* ptr = nullptr;
   int32_t* idx = nullptr;
   double* v64 = nullptr;
@@ -114,6 +115,10 @@ struct SpmmArgs {
   // Early exit: when non-NULL and *skip == 0 (no active RHS) the kernel does
   // nothing (lets the host run one iteration ahead of its convergence check).
   const int32_t* skip = nullptr;
+  // Tile: entry lanes per row (1, 2, 4, 8, 16; 0 = 1) and columns per
+  // thread (0 = one 16-byte vector; 2x that when C allows); see spmm_kernel.
+  int32_t kl = 0;
+  int32_t cpt = 0;
   DotArgs dot;
 };
 
@@ -156,5 +161,9 @@ int64_t launch_count();
 
 int num_sms();
 int max_grid_blocks();  // blocks for grid-stride kernels (SMs x resident blocks)
+
+// Full-wave grid for a 256-thread kernel: SMs x the blocks of this kernel
+// that fit on one SM (registers, shared memory), looked up once per kernel.
+int resident_grid(const void* kernel, size_t smem_bytes);
 
 }  // namespace amgsym

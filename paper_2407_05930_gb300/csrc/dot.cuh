@@ -82,18 +82,60 @@ __device__ __forceinline__ void dot_finalize_rhs(const DotArgs& d, const double*
 }
 
 // Block + grid reduction.  part[q] is this thread's partial for column
-// c0 + q (ignored when !has_cols).  Shared scratch: kBlock * CPT + 2 * 256 doubles.
+// c0 + q (zero when !has_cols).  Threads of one row slot are S consecutive
+// lanes; when S is a power of two <= 32 the row slots of a warp are first
+// combined with xor shuffles (lanes l, l^S, l^2S, ... share their columns),
+// so shared memory holds one partial per warp and column; otherwise every
+// slot gets its own line.  Shared scratch (dynamic): dot_smem_doubles(...).
+// Every sum runs in a fixed assignment of threads to terms, so the order of
+// additions, and the result, never varies from run to run.
+__host__ __device__ inline int dot_smem_doubles(int S, int rows_pb, int C) {
+  const bool pow2 = S > 0 && (S & (S - 1)) == 0 && S <= 32;
+  const int lines = pow2 ? kBlock / 32 : rows_pb;
+  return lines * C + kBlock + C;
+}
+
 template <int CPT>
-__device__ __forceinline__ void block_dot(const DotArgs& d, const double (&part)[CPT], int c0, bool has_cols,
-                                          int rloc, int rows_pb, int C, double* sm) {
-  if (has_cols) {
+__device__ __forceinline__ void block_dot(const DotArgs& d, double (&part)[CPT], int c0, bool has_cols,
+                                          int rloc, int rows_pb, int S, int C, double* sm) {
+  const bool pow2 = (S & (S - 1)) == 0 && S <= 32;
+  int lines;
+  if (pow2) {
+    for (int off = S; off < 32; off <<= 1) {
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) sm[rloc * C + c0 + q] = part[q];
+      for (int q = 0; q < CPT; ++q) part[q] += __shfl_xor_sync(0xffffffffu, part[q], off);
+    }
+    lines = kBlock / 32;
+    const int lane = threadIdx.x & 31;
+    if (has_cols && lane < S) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) sm[(threadIdx.x >> 5) * C + c0 + q] = part[q];
+    }
+  } else {
+    lines = rows_pb;
+    if (has_cols) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) sm[rloc * C + c0 + q] = part[q];
+    }
+  }
+  __syncthreads();
+  const int slices = blockDim.x / C;  // C <= 256 = blockDim
+  double* red = sm + lines * C;       // [slices][C], <= 256 doubles
+  if ((int)threadIdx.x < slices * C) {
+    const int c = threadIdx.x % C, sl = threadIdx.x / C;
+    double t0 = 0.0, t1 = 0.0;
+    int r = sl;
+    for (; r + slices < lines; r += 2 * slices) {
+      t0 += sm[r * C + c];
+      t1 += sm[(r + slices) * C + c];
+    }
+    if (r < lines) t0 += sm[r * C + c];
+    red[sl * C + c] = t0 + t1;
   }
   __syncthreads();
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
     double t = 0.0;
-    for (int r = 0; r < rows_pb; ++r) t += sm[r * C + c];
+    for (int sl = 0; sl < slices; ++sl) t += red[sl * C + c];
     d.sc.partials[(int64_t)blockIdx.x * C + c] = t;
   }
   __threadfence();
@@ -103,16 +145,22 @@ __device__ __forceinline__ void block_dot(const DotArgs& d, const double (&part)
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  const int slices = blockDim.x / C;  // C <= 256 = blockDim
-  double* red = sm;                   // [slices][C]
   if ((int)threadIdx.x < slices * C) {
     const int c = threadIdx.x % C, sl = threadIdx.x / C;
-    double t = 0.0;
-    for (int b = sl; b < (int)gridDim.x; b += slices) t += __ldcg(d.sc.partials + (int64_t)b * C + c);
-    red[sl * C + c] = t;
+    const int nblk = (int)gridDim.x;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    int b = sl;
+    for (; b + 3 * slices < nblk; b += 4 * slices) {
+      t0 += __ldcg(d.sc.partials + (int64_t)b * C + c);
+      t1 += __ldcg(d.sc.partials + (int64_t)(b + slices) * C + c);
+      t2 += __ldcg(d.sc.partials + (int64_t)(b + 2 * slices) * C + c);
+      t3 += __ldcg(d.sc.partials + (int64_t)(b + 3 * slices) * C + c);
+    }
+    for (; b < nblk; b += slices) t0 += __ldcg(d.sc.partials + (int64_t)b * C + c);
+    red[sl * C + c] = (t0 + t1) + (t2 + t3);
   }
   __syncthreads();
-  double* colsum = sm + kBlock;  // [C]
+  double* colsum = sm;  // [C]
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
     double t = 0.0;
     for (int sl = 0; sl < slices; ++sl) t += red[sl * C + c];

@@ -504,6 +504,60 @@ static std::vector<double> dense_inverse(const Csr& A) {
   return inv;
 }
 
+// Sparsified Galerkin operator: off-diagonal entries with |a_ij| <
+// theta sqrt(a_ii a_jj) (a symmetric test) are removed and added to the
+// diagonal of their row, which keeps row sums and symmetry.  Removing a
+// negative coupling of a diagonally dominant M-matrix keeps it weakly
+// diagonally dominant, so the operator stays positive definite.
+static Csr sparsify(const Csr& A, double theta) {
+  if (theta <= 0.0) return A;
+  const int64_t n = A.rows;
+  std::vector<double> diag(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) diag[i] = find(A, i, (int32_t)i);
+  Csr B;
+  B.rows = A.rows;
+  B.cols = A.cols;
+  B.ptr.assign(n + 1, 0);
+  std::vector<double> lump(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t cnt = 0;
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+      const int32_t j = A.idx[e];
+      const double thr = theta * std::sqrt(std::fabs(diag[i] * diag[j]));
+      if (j == i || std::fabs(A.val[e]) >= thr)
+        ++cnt;
+      else
+        lump[i] += A.val[e];
+    }
+    B.ptr[i + 1] = B.ptr[i] + cnt;
+  }
+  B.idx.resize(B.ptr[n]);
+  B.val.resize(B.ptr[n]);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t w = B.ptr[i];
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+      const int32_t j = A.idx[e];
+      const double thr = theta * std::sqrt(std::fabs(diag[i] * diag[j]));
+      if (j == i) {
+        B.idx[w] = j;
+        B.val[w++] = A.val[e] + lump[i];
+      } else if (std::fabs(A.val[e]) >= thr) {
+        B.idx[w] = j;
+        B.val[w++] = A.val[e];
+      }
+    }
+  }
+  return B;
+}
+
+// (A + A^T) / 2 for a matrix with a symmetric pattern and sorted rows (the
+// Galerkin product is symmetric up to rounding); unchanged otherwise.
+static void symmetrize(Csr& A) {
+  Csr T = transpose(A);
+  if (T.ptr != A.ptr || T.idx != A.idx) return;
+  for (int64_t e = 0; e < A.nnz(); ++e) A.val[e] = 0.5 * (A.val[e] + T.val[e]);
+}
+
 static constexpr int64_t kDenseLimit = 4096;
 
 void build_hierarchy(const Csr& A0, const amgsym_opts& o, HostHierarchy& H) {
@@ -537,6 +591,8 @@ void build_hierarchy(const Csr& A0, const amgsym_opts& o, HostHierarchy& H) {
     L.R = transpose(L.P);
     Csr AP = spgemm(L.A, L.P);
     Csr Ac = spgemm(L.R, AP);
+    symmetrize(Ac);
+    Ac = sparsify(Ac, o.coarse_drop);
     H.levels.emplace_back();
     H.levels[lev + 1].A = std::move(Ac);
   }

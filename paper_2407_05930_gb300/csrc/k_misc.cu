@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 
 #include "device.h"
 #include "dot.cuh"
@@ -26,8 +28,26 @@ int num_sms() {
   return g_sms;
 }
 
-// Grid-stride kernels run 8 resident 256-thread blocks per SM (2048 threads).
+// Grid-stride kernels run at most 8 resident 256-thread blocks per SM (2048 threads).
 int max_grid_blocks() { return num_sms() * 8; }
+
+int resident_grid(const void* kernel, size_t smem_bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(kernel, smem_bytes);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem_bytes) != cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();  // not cached: fall back to the static bound this time
+    return max_grid_blocks();
+  }
+  const int g = num_sms() * std::min(per_sm, 8);
+  cache[key] = g;
+  return g;
+}
 
 static int grid_for(int64_t work, int per_block) {
   int64_t g = (work + per_block - 1) / per_block;
@@ -149,6 +169,11 @@ void launch_transform_bwd(const void* xhat, VecType it, int32_t nrhs, const int3
 // thread mapping is the SpMM's (thread owns CPT columns of a row slot) so the
 // fused dot reduction is shared.
 
+template <typename T, int N>
+struct alignas(sizeof(T) * N) VecM {
+  T v[N];
+};
+
 template <typename T>
 struct DotAcc {
   using type = float;
@@ -164,47 +189,67 @@ __global__ void __launch_bounds__(kBlock) cg_update1_kernel(int64_t rows, int32_
                                                             const T* __restrict__ q, DotArgs dot,
                                                             const int32_t* skip) {
   using DT = typename DotAcc<T>::type;
+  using V = VecM<T, CPT>;
   if (skip && *skip == 0) return;
   const int TPR = C / CPT;
   const int rows_pb = kBlock / TPR;
   const int rloc = threadIdx.x / TPR;
   const int c0 = (threadIdx.x % TPR) * CPT;
   const bool has_cols = rloc < rows_pb;
-  double al[CPT];
+  T al[CPT];
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) al[k] = dot.sc.alpha[c0 + k];
+  for (int k = 0; k < CPT; ++k) al[k] = (T)dot.sc.alpha[c0 + k];
   DT part[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) part[k] = (DT)0;
   if (has_cols) {
     for (int64_t row = blockIdx.x * (int64_t)rows_pb + rloc; row < rows; row += (int64_t)gridDim.x * rows_pb) {
       const int64_t o = row * C + c0;
+      V xv = *reinterpret_cast<const V*>(x + o);
+      V rv = *reinterpret_cast<const V*>(r + o);
+      const V pv = *reinterpret_cast<const V*>(p + o);
+      const V qv = *reinterpret_cast<const V*>(q + o);
 #pragma unroll
       for (int k = 0; k < CPT; ++k) {
-        const T a = (T)al[k];
-        x[o + k] = x[o + k] + a * p[o + k];
-        const T rn = r[o + k] - a * q[o + k];
-        r[o + k] = rn;
-        part[k] += (DT)rn * (DT)rn;
+        xv.v[k] = xv.v[k] + al[k] * pv.v[k];
+        rv.v[k] = rv.v[k] - al[k] * qv.v[k];
+        part[k] += (DT)rv.v[k] * (DT)rv.v[k];
       }
+      *reinterpret_cast<V*>(x + o) = xv;
+      *reinterpret_cast<V*>(r + o) = rv;
     }
   }
   if (HAS_DOT) {
-    __shared__ double sm[kBlock * CPT + 2 * kBlock];
+    extern __shared__ double sm[];
     double pd[CPT];
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) pd[k] = (double)part[k];
-    block_dot<CPT>(dot, pd, c0, has_cols, rloc, rows_pb, C, sm);
+    for (int k = 0; k < CPT; ++k) pd[k] = has_cols ? (double)part[k] : 0.0;
+    block_dot<CPT>(dot, pd, c0, has_cols, rloc, rows_pb, TPR, C, sm);
   }
+}
+
+template <typename T, int CPT>
+static void update1_c(int64_t rows, int32_t C, void* x, void* r, const void* p, const void* q, const DotArgs& dot,
+                      cudaStream_t st, const int32_t* skip) {
+  const int rows_pb = kBlock / (C / CPT);
+  const size_t smem = sizeof(double) * (size_t)dot_smem_doubles(C / CPT, rows_pb, C);
+  int g = grid_for(rows, rows_pb > 0 ? rows_pb : 1);
+  g = std::min(g, resident_grid((const void*)cg_update1_kernel<T, CPT, true>, smem));
+  if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
+  cg_update1_kernel<T, CPT, true><<<g, kBlock, smem, st>>>(rows, C, static_cast<T*>(x), static_cast<T*>(r),
+                                                        static_cast<const T*>(p), static_cast<const T*>(q), dot, skip);
 }
 
 template <typename T>
 static void update1_t(int64_t rows, int32_t C, void* x, void* r, const void* p, const void* q, const DotArgs& dot,
                       cudaStream_t st, const int32_t* skip) {
-  int g = grid_for(rows, kBlock / C > 0 ? kBlock / C : 1);
-  if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
-  cg_update1_kernel<T, 1, true><<<g, kBlock, 0, st>>>(rows, C, static_cast<T*>(x), static_cast<T*>(r),
-                                                      static_cast<const T*>(p), static_cast<const T*>(q), dot, skip);
+  constexpr int V = 16 / (int)sizeof(T);
+  if (V >= 4 && C % 4 == 0)
+    update1_c<T, (V >= 4 ? 4 : 1)>(rows, C, x, r, p, q, dot, st, skip);
+  else if (C % 2 == 0)
+    update1_c<T, 2>(rows, C, x, r, p, q, dot, st, skip);
+  else
+    update1_c<T, 1>(rows, C, x, r, p, q, dot, st, skip);
 }
 
 void launch_cg_update1(VecType vt, int64_t rows, int32_t C, void* x, void* r, const void* p, const void* q,
@@ -216,26 +261,58 @@ void launch_cg_update1(VecType vt, int64_t rows, int32_t C, void* x, void* r, co
     update1_t<float>(rows, C, x, r, p, q, dot, st, skip);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlock) cg_update2_kernel(int64_t count, int32_t C, T* __restrict__ p,
+// p = z + beta p, CPT columns per thread with vector loads.
+template <typename T, int CPT>
+__global__ void __launch_bounds__(kBlock) cg_update2_kernel(int64_t rows, int32_t C, T* __restrict__ p,
                                                             const T* __restrict__ z, const double* __restrict__ beta,
                                                             const int32_t* skip) {
+  using V = VecM<T, CPT>;
   if (skip && *skip == 0) return;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-    const T b = (T)beta[e % C];
-    p[e] = z[e] + b * p[e];
+  const int TPR = C / CPT;
+  const int rows_pb = kBlock / TPR;
+  const int rloc = threadIdx.x / TPR;
+  const int c0 = (threadIdx.x % TPR) * CPT;
+  if (rloc >= rows_pb) return;
+  T b[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) b[k] = (T)beta[c0 + k];
+  for (int64_t row = blockIdx.x * (int64_t)rows_pb + rloc; row < rows; row += (int64_t)gridDim.x * rows_pb) {
+    const int64_t o = row * C + c0;
+    V pv = *reinterpret_cast<const V*>(p + o);
+    const V zv = *reinterpret_cast<const V*>(z + o);
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) pv.v[k] = zv.v[k] + b[k] * pv.v[k];
+    *reinterpret_cast<V*>(p + o) = pv;
   }
+}
+
+template <typename T, int CPT>
+static void update2_c(int64_t rows, int32_t C, void* p, const void* z, const double* beta, cudaStream_t st,
+                      const int32_t* skip) {
+  const int rows_pb = kBlock / (C / CPT);
+  const int g = grid_for(rows, rows_pb > 0 ? rows_pb : 1);
+  cg_update2_kernel<T, CPT><<<g, kBlock, 0, st>>>(rows, C, static_cast<T*>(p), static_cast<const T*>(z), beta, skip);
+}
+
+template <typename T>
+static void update2_t(int64_t rows, int32_t C, void* p, const void* z, const double* beta, cudaStream_t st,
+                      const int32_t* skip) {
+  constexpr int V = 16 / (int)sizeof(T);
+  if (V >= 4 && C % 4 == 0)
+    update2_c<T, (V >= 4 ? 4 : 1)>(rows, C, p, z, beta, st, skip);
+  else if (C % 2 == 0)
+    update2_c<T, 2>(rows, C, p, z, beta, st, skip);
+  else
+    update2_c<T, 1>(rows, C, p, z, beta, st, skip);
 }
 
 void launch_cg_update2(VecType vt, int64_t rows, int32_t C, void* p, const void* z, const double* beta,
                        cudaStream_t st, const int32_t* skip) {
   count_launch();
-  const int64_t count = rows * C;
-  const int g = grid_for(count, kBlock);
   if (vt == VEC_F64)
-    cg_update2_kernel<double><<<g, kBlock, 0, st>>>(count, C, static_cast<double*>(p), static_cast<const double*>(z), beta, skip);
+    update2_t<double>(rows, C, p, z, beta, st, skip);
   else
-    cg_update2_kernel<float><<<g, kBlock, 0, st>>>(count, C, static_cast<float*>(p), static_cast<const float*>(z), beta, skip);
+    update2_t<float>(rows, C, p, z, beta, st, skip);
 }
 
 template <typename T>
@@ -296,8 +373,8 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(int64_t rows, int32_t C, co
   if (has_cols)
     for (int64_t row = blockIdx.x * (int64_t)rows_pb + rloc; row < rows; row += (int64_t)gridDim.x * rows_pb)
       part[0] += (double)a[row * C + c0] * (double)b[row * C + c0];
-  __shared__ double sm[kBlock + 2 * kBlock];
-  block_dot<1>(dot, part, c0, has_cols, rloc, rows_pb, C, sm);
+  extern __shared__ double sm[];
+  block_dot<1>(dot, part, c0, has_cols, rloc, rows_pb, TPR, C, sm);
 }
 
 void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,
@@ -305,10 +382,11 @@ void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* 
   count_launch();
   int g = grid_for(rows, kBlock / C > 0 ? kBlock / C : 1);
   if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
+  const size_t smem = sizeof(double) * (size_t)dot_smem_doubles(C, kBlock / C, C);
   if (vt == VEC_F64)
-    dot_kernel<double><<<g, kBlock, 0, st>>>(rows, C, static_cast<const double*>(a), static_cast<const double*>(b), dot, skip);
+    dot_kernel<double><<<g, kBlock, smem, st>>>(rows, C, static_cast<const double*>(a), static_cast<const double*>(b), dot, skip);
   else
-    dot_kernel<float><<<g, kBlock, 0, st>>>(rows, C, static_cast<const float*>(a), static_cast<const float*>(b), dot, skip);
+    dot_kernel<float><<<g, kBlock, smem, st>>>(rows, C, static_cast<const float*>(a), static_cast<const float*>(b), dot, skip);
 }
 
 // ---------------------------------------------------------------------------

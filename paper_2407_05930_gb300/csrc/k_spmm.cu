@@ -57,9 +57,10 @@ __device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 v) {
   return (double)__bfloat162float(v);
 }
 
-// Vector of N consecutive T (N * sizeof(T) <= 16 bytes, naturally aligned).
+// Vector of N consecutive T, aligned to its size up to 32 bytes (a 32-byte
+// vector is one 256-bit access where the hardware has it, else two 16-byte ones).
 template <typename T, int N>
-struct alignas(sizeof(T) * N) Vec {
+struct alignas(sizeof(T) * N <= 32 ? sizeof(T) * N : 32) Vec {
   T v[N];
 };
 
@@ -94,17 +95,27 @@ struct ComputeOf<double, double> {
   using type = double;
 };
 
-template <typename MT, typename XT, typename OT, int CPT, bool HAS_DOT, bool HAS_IFACE>
-__global__ void __launch_bounds__(kBlock) spmm_kernel(SpmmArgs a) {
+// Thread layout.  A row is served by S = TPC * KL threads: TPC column
+// threads (each owning CPT consecutive columns, TPC = C / CPT) times KL entry
+// lanes (lane e takes the row's entries e, e + KL, ...).  The KL partial sums
+// are combined with warp shuffles (S divides 32 when KL > 1), and entry lane 0
+// runs the epilogue.  KL > 1 keeps several gathers of one row in flight, which
+// is what hides the ptr -> idx -> X latency chain of short rows and spreads the
+// long rows of the coarse levels over many lanes.
+template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE>
+__global__ void __launch_bounds__(kBlock, 8) spmm_kernel(SpmmArgs a) {
   using CT = typename ComputeOf<MT, XT>::type;
   using DT = typename AccOf<XT>::type;  // per-thread dot partial type
-  if (a.skip && *a.skip == 0) return;  // uniform over the grid
+  if (a.skip && *a.skip == 0) return;   // uniform over the grid
   const int C = a.C;
-  const int TPR = C / CPT;
-  const int rows_pb = kBlock / TPR;
-  const int rloc = threadIdx.x / TPR;
-  const int c0 = (threadIdx.x % TPR) * CPT;
-  const bool has_cols = rloc < rows_pb;
+  const int TPC = C / CPT;
+  const int S = TPC * KL;
+  const int rows_pb = kBlock / S;
+  const int g = threadIdx.x / S;
+  const int w = threadIdx.x - g * S;
+  const int e = KL > 1 ? w / TPC : 0;
+  const int c0 = (w - e * TPC) * CPT;
+  const bool slot_ok = g < rows_pb;
   const MT* __restrict__ val = static_cast<const MT*>(a.val);
   const XT* __restrict__ X = static_cast<const XT*>(a.X);
   // Y may alias Z (in-place update z += ...); each row reads Z before writing Y.
@@ -117,17 +128,22 @@ __global__ void __launch_bounds__(kBlock) spmm_kernel(SpmmArgs a) {
 #pragma unroll
   for (int q = 0; q < CPT; ++q) dpart[q] = (DT)0;
 
-  if (has_cols) {
-    for (int row = blockIdx.x * rows_pb + rloc; row < a.rows; row += gridDim.x * rows_pb) {
-      CT acc[CPT];
+  // Grid-stride over row slots: a wave of blocks sweeps one contiguous window
+  // of rows, so the far neighbours one block gathers were recently brought
+  // into L2 by another.  The trip count is block-uniform (the shuffles need
+  // every lane of the warp).
+  for (int base = blockIdx.x * rows_pb; base < a.rows; base += gridDim.x * rows_pb) {
+    const int row = base + g;
+    const bool live = slot_ok && row < a.rows;
+    CT acc[CPT];
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
+    for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
+    if (live) {
       const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
-      int k = kb;
-      // two entries per step for memory-level parallelism
-      for (; k + 1 < ke; k += 2) {
-        const int j0 = __ldg(idx + k), j1 = __ldg(idx + k + 1);
-        const CT m0 = cvt<CT>(val[k]), m1 = cvt<CT>(val[k + 1]);
+      int k = kb + e;
+      for (; k + KL < ke; k += 2 * KL) {
+        const int j0 = __ldg(idx + k), j1 = __ldg(idx + k + KL);
+        const CT m0 = cvt<CT>(val[k]), m1 = cvt<CT>(val[k + KL]);
         const Vec<XT, CPT> x0 = ldv<XT, CPT>(X + (int64_t)j0 * C + c0);
         const Vec<XT, CPT> x1 = ldv<XT, CPT>(X + (int64_t)j1 * C + c0);
 #pragma unroll
@@ -143,23 +159,32 @@ __global__ void __launch_bounds__(kBlock) spmm_kernel(SpmmArgs a) {
 #pragma unroll
         for (int q = 0; q < CPT; ++q) acc[q] = fma(m0, (CT)x0.v[q], acc[q]);
       }
-      if (HAS_IFACE) {
-        const uint32_t w = __ldg(a.imask + (row >> 5));
+      if (HAS_IFACE && e == 0) {
+        const uint32_t wd = __ldg(a.imask + (row >> 5));
         const uint32_t bit = 1u << (row & 31);
-        if (w & bit) {
-          const int f = __ldg(a.iprefix + (row >> 5)) + __popc(w & (bit - 1u));
+        if (wd & bit) {
+          const int f = __ldg(a.iprefix + (row >> 5)) + __popc(wd & (bit - 1u));
           const CT* __restrict__ iv = static_cast<const CT*>(a.ival);
-          for (int e = __ldg(a.iptr + f); e < __ldg(a.iptr + f + 1); ++e) {
-            const int j = __ldg(a.icol + e);
+          for (int ee = __ldg(a.iptr + f); ee < __ldg(a.iptr + f + 1); ++ee) {
+            const int j = __ldg(a.icol + ee);
             const Vec<XT, CPT> xv = ldv<XT, CPT>(X + (int64_t)j * C + c0);
 #pragma unroll
             for (int q = 0; q < CPT; ++q) {
               const int blk = (c0 + q) % a.nb;
-              acc[q] = fma(iv[(int64_t)e * a.nb + blk], (CT)xv.v[q], acc[q]);
+              acc[q] = fma(iv[(int64_t)ee * a.nb + blk], (CT)xv.v[q], acc[q]);
             }
           }
         }
       }
+    }
+    if (KL > 1) {
+#pragma unroll
+      for (int off = KL / 2; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off * TPC);
+      }
+    }
+    if (live && e == 0) {
       Vec<OT, CPT> out;
       if (a.beta != 0.0) {
         const Vec<XT, CPT> zv = ldv<XT, CPT>(Z + (int64_t)row * C + c0);
@@ -191,42 +216,70 @@ __global__ void __launch_bounds__(kBlock) spmm_kernel(SpmmArgs a) {
     }
   }
   if (HAS_DOT) {
-    __shared__ double sm[kBlock * CPT + 2 * kBlock];
+    extern __shared__ double sm[];
     double part[CPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) part[q] = (double)dpart[q];
-    block_dot<CPT>(a.dot, part, c0, has_cols, rloc, rows_pb, C, sm);
+    for (int q = 0; q < CPT; ++q) part[q] = (slot_ok && e == 0) ? (double)dpart[q] : 0.0;
+    block_dot<CPT>(a.dot, part, c0, slot_ok && e == 0, g, rows_pb, S, C, sm);
   }
 }
 
-template <typename MT, typename XT, typename OT, int CPT>
-static void launch_t(const SpmmArgs& a, cudaStream_t st) {
-  const int TPR = a.C / CPT;
-  const int rows_pb = kBlock / TPR;
+template <typename MT, typename XT, typename OT, int CPT, int KL>
+static void launch_k(const SpmmArgs& a, cudaStream_t st) {
+  const int TPC = a.C / CPT;
+  const int rows_pb = kBlock / (TPC * KL);
   int64_t need = ((int64_t)a.rows + rows_pb - 1) / rows_pb;
   int grid = (int)std::min<int64_t>(need, (int64_t)max_grid_blocks());
   if (grid < 1) grid = 1;
   const bool dot = a.dot.mode != DOT_NONE;
   const bool ifc = a.imask != nullptr;
   count_launch();
+  // one full wave of resident blocks (the register count differs per variant)
+  auto run = [&](auto kern, size_t smem) {
+    int g = std::min(grid, resident_grid((const void*)kern, smem));
+    if (dot && (int64_t)g * a.C > a.dot.sc.partial_cap) g = (int)(a.dot.sc.partial_cap / a.C);
+    kern<<<g, kBlock, smem, st>>>(a);
+  };
   if (dot) {
-    if ((int64_t)grid * a.C > a.dot.sc.partial_cap) grid = (int)(a.dot.sc.partial_cap / a.C);
+    const size_t smem = sizeof(double) * (size_t)dot_smem_doubles(TPC * KL, rows_pb, a.C);
     if (ifc)
-      spmm_kernel<MT, XT, OT, CPT, true, true><<<grid, kBlock, 0, st>>>(a);
+      run(spmm_kernel<MT, XT, OT, CPT, KL, true, true>, smem);
     else
-      spmm_kernel<MT, XT, OT, CPT, true, false><<<grid, kBlock, 0, st>>>(a);
+      run(spmm_kernel<MT, XT, OT, CPT, KL, true, false>, smem);
   } else {
     if (ifc)
-      spmm_kernel<MT, XT, OT, CPT, false, true><<<grid, kBlock, 0, st>>>(a);
+      run(spmm_kernel<MT, XT, OT, CPT, KL, false, true>, 0);
     else
-      spmm_kernel<MT, XT, OT, CPT, false, false><<<grid, kBlock, 0, st>>>(a);
+      run(spmm_kernel<MT, XT, OT, CPT, KL, false, false>, 0);
+  }
+}
+
+template <typename MT, typename XT, typename OT, int CPT>
+static void launch_t(const SpmmArgs& a, cudaStream_t st) {
+  const int TPC = a.C / CPT;
+  // entry lanes: only with a power-of-two column-thread count, and S <= 32
+  int kl = a.kl > 0 ? a.kl : 1;
+  if (TPC & (TPC - 1)) kl = 1;
+  while (kl > 1 && TPC * kl > 32) kl >>= 1;
+  switch (kl) {
+    case 1: launch_k<MT, XT, OT, CPT, 1>(a, st); break;
+    case 2: launch_k<MT, XT, OT, CPT, 2>(a, st); break;
+    case 4: launch_k<MT, XT, OT, CPT, 4>(a, st); break;
+    case 8: launch_k<MT, XT, OT, CPT, 8>(a, st); break;
+    default: launch_k<MT, XT, OT, CPT, 16>(a, st); break;
   }
 }
 
 template <typename MT, typename XT, typename OT>
 static void launch_c(const SpmmArgs& a, cudaStream_t st) {
+  // V: elements of the narrower of X / Y in one 16-byte vector
   constexpr int V = 16 / (int)sizeof(XT) < 16 / (int)sizeof(OT) ? 16 / (int)sizeof(XT) : 16 / (int)sizeof(OT);
-  if (V >= 4 && a.C % 4 == 0 && a.C / 4 <= kBlock)
+  const int want = a.cpt > 0 ? a.cpt : V;
+  if (want >= 2 * V && V == 4 && a.C % 8 == 0 && a.C / 8 <= kBlock)
+    launch_t<MT, XT, OT, 8>(a, st);
+  else if (want >= 2 * V && V == 2 && a.C % 4 == 0 && a.C / 4 <= kBlock)
+    launch_t<MT, XT, OT, 4>(a, st);
+  else if (V >= 4 && a.C % 4 == 0 && a.C / 4 <= kBlock)
     launch_t<MT, XT, OT, 4>(a, st);
   else if (V >= 2 && a.C % 2 == 0 && a.C / 2 <= kBlock)
     launch_t<MT, XT, OT, 2>(a, st);

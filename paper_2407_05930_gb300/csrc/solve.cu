@@ -10,7 +10,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <set>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -58,8 +61,17 @@ struct GraphCache {
   GraphKey key;
 };
 
+// SpMM tile (columns per thread, entry lanes per row) chosen by the tuner for
+// one matrix, column count and precision combination.
+struct Tile {
+  int cpt = 0, kl = 0;
+};
+using TileKey = std::tuple<const void*, int32_t, int, int, int>;  // matrix idx array, C, mt, xt, ot
+
 struct Device {
   int device_id = 0;
+  std::map<TileKey, Tile> tiles;
+  std::set<std::tuple<int32_t, int, int>> tuned;  // (C, vt, mt) already tuned
   int precisions = 3;
   int nu = 1;
   int32_t s = 0, nb = 1;
@@ -106,6 +118,7 @@ static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions
   D.rows = (int32_t)M.rows;
   D.cols = (int32_t)M.cols;
   D.nnz = M.nnz();
+  D.avg_row = M.rows > 0 ? (double)M.nnz() / (double)M.rows : 0.0;
   std::vector<int32_t> p32(M.ptr.begin(), M.ptr.end());
   D.ptr = upload(owner, p32.data(), (int64_t)p32.size());
   D.idx = upload(owner, M.idx.data(), D.nnz);
@@ -287,7 +300,20 @@ struct Ctx {
   bool finest_hat;  // V-cycle level-0 residual with A^_i
   cudaStream_t st;
   const int32_t* skip = nullptr;  // early-exit flag (active RHS count) of the PCG loop
+  bool tune = false;              // run the tile autotuner before the first PCG loop
 };
+
+// Entry lanes per row: one lane for short rows (fine-level stencils, where
+// the L1-resident neighbours keep the gathers cheap), then about 5 entries per
+// lane for the longer rows of the coarse Galerkin operators, at most 32
+// threads per row.
+static int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt) {
+  const int cpt = xt == VEC_F64 ? 2 : 4;
+  const int tpc = (C % cpt == 0) ? C / cpt : C;
+  int kl = 1;
+  while (kl < 16 && M.avg_row >= 10.0 * kl && tpc * kl * 2 <= 32) kl *= 2;
+  return kl;
+}
 
 static void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X, void* Y,
                  double alpha, double beta, const void* Z, bool iface, const DotArgs* dot) {
@@ -314,8 +340,94 @@ static void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType 
   }
   if (dot) a.dot = *dot;
   a.skip = c.skip;
+  auto it = c.D->tiles.find(TileKey{M.idx, c.C, (int)mt, (int)xt, (int)ot});
+  if (it != c.D->tiles.end()) {
+    a.kl = it->second.kl;
+    a.cpt = it->second.cpt;
+  } else {
+    a.kl = entry_lanes(M, c.C, xt);
+  }
   launch_spmm(mt, xt, ot, a, c.st);
   check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Tile autotuner.  For every sparse matrix of the V-cycle and the reduced
+// operator, at the column count and precisions of the solve, time each
+// candidate tile -- columns per thread (one or two 16-byte vectors) times
+// entry lanes per row (1..16) -- with CUDA events and keep the fastest.  It
+// runs once per (C, precision) before the PCG graph is captured, on scratch
+// level vectors (their contents do not matter for timing).  Results are
+// bit-reproducible for a fixed tile choice; the choice itself is timing-based.
+static void tune_tiles(const Ctx& c) {
+  Device* D = c.D;
+  auto key = std::make_tuple(c.C, (int)c.vt, (int)c.mt);
+  if (D->tuned.count(key)) return;
+  PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
+  const size_t es = c.vt == VEC_F64 ? 8 : 4;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (size_t l = 0; l < D->lv.size(); ++l) {
+    if (W.lw[l].t) CK(cudaMemsetAsync(W.lw[l].t, 0, es * (size_t)D->lv[l].n * c.C, c.st));
+    if (W.lw[l].z) CK(cudaMemsetAsync(W.lw[l].z, 0, es * (size_t)D->lv[l].n * c.C, c.st));
+    if (W.lw[l].r) CK(cudaMemsetAsync(W.lw[l].r, 0, es * (size_t)D->lv[l].n * c.C, c.st));
+  }
+  struct Job {
+    const DevCsr* M;
+    ValType mt;
+    const void* X;
+    void* Y;
+    bool iface;
+  };
+  std::vector<Job> jobs;
+  const ValType kmt = c.vt == VEC_F64 ? VAL_F64 : VAL_F32;
+  jobs.push_back({&D->Ainn, kmt, W.lw[0].t, W.lw[0].r, true});  // reduced operator
+  for (size_t l = 0; l + 1 < D->lv.size(); ++l) {
+    const DevLevel& L = D->lv[l];
+    if (L.cinv) break;
+    jobs.push_back({&L.A, c.mt, W.lw[l].t, W.lw[l].r, false});
+    jobs.push_back({&L.G, c.mt, W.lw[l].t, W.lw[l].r, false});
+    jobs.push_back({&L.Gt, c.mt, W.lw[l].t, W.lw[l].r, false});
+    jobs.push_back({&L.R, c.mt, W.lw[l].r, W.lw[l + 1].y, false});
+    jobs.push_back({&L.P, c.mt, W.lw[l + 1].z, W.lw[l].t, false});
+  }
+  const int vmax = c.vt == VEC_F64 ? 2 : 4;
+  for (const Job& j : jobs) {
+    if (!j.M->vals(j.mt)) continue;
+    Tile best;
+    float best_ms = 1e30f;
+    for (int cm = 1; cm <= 2; ++cm) {
+      const int cpt = vmax * cm;
+      if (c.C % cpt) continue;
+      const int tpc = c.C / cpt;
+      for (int kl = 1; kl <= 16; kl *= 2) {
+        if (kl > 1 && ((tpc & (tpc - 1)) || tpc * kl > 32)) break;
+        Ctx cc = c;
+        D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)c.vt}] = Tile{cpt, kl};
+        spmm(cc, *j.M, j.mt, c.vt, c.vt, j.X, j.Y, 1.0, 0.0, nullptr, j.iface, nullptr);  // warm-up
+        CK(cudaEventRecord(e0, c.st));
+        const int reps = 3;
+        for (int r = 0; r < reps; ++r) spmm(cc, *j.M, j.mt, c.vt, c.vt, j.X, j.Y, 1.0, 0.0, nullptr, j.iface, nullptr);
+        CK(cudaEventRecord(e1, c.st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms * 0.97f) {  // prefer the earlier (simpler) tile on near-ties
+          best_ms = ms;
+          best = Tile{cpt, kl};
+        }
+      }
+    }
+    if (best.cpt > 0) {
+      // the same tile serves every output type / fused variant of this matrix
+      D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)c.vt}] = best;
+      D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)VEC_F32}] = best;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  D->tuned.insert(key);
 }
 
 // One V(nu, nu) cycle at level l: z = M_l^{-1} y (Alg. "apply" shape with the
@@ -404,6 +516,7 @@ static void read_status(Device* D, const DevScalars& sc, cudaStream_t st, int32_
 static int pcg_loop(const Ctx& c0, PrecWork& W, const DevScalars& sc, int32_t nrhs, double tol, int maxit,
                     bool use_graph, int graph_mode, bool* breakdown) {
   Device* D = c0.D;
+  if (c0.tune) tune_tiles(c0);
   Ctx c = c0;
   c.skip = sc.status;
   GraphKey graph_key;
@@ -507,6 +620,7 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
   ensure_work(D, nrhs, vt);
   const int32_t C = nrhs * D->nb;
   Ctx c{D, C, vt, vmt, o.finest_hat != 0, st};
+  c.tune = o.tune != 0;
   Ctx c64{D, C, VEC_F64, VAL_F64, false, st};
   // 64-bit work is needed for the FP64 path; the mixed path uses bh/xh only.
   PrecWork& W = mixed ? D->w32 : D->w64;

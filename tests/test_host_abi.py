@@ -139,10 +139,11 @@ def _csr(t):
     return sp.csr_matrix((v, ci, rp), shape=shape)
 
 
-def test_hierarchy_structure():
+@pytest.mark.parametrize("drop", [0.0, 0.01])
+def test_hierarchy_structure(drop):
     N, s = (32, 32, 32), 3
     g = gaussian_logk(N, s, seed=3, corr=4.0)
-    P = amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, coarse_max=128)
+    P = amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, coarse_max=128, coarse_drop=drop)
     L = P.num_levels()
     assert L >= 3
     A0 = _csr(P.level_matrix(0, "A"))
@@ -153,9 +154,19 @@ def test_hierarchy_structure():
         Pm = _csr(P.level_matrix(l, "P"))
         G = _csr(P.level_matrix(l, "G"))
         Ac = _csr(P.level_matrix(l + 1, "A"))
-        # Galerkin coarse operator R A P with R = P^T
+        # Galerkin coarse operator R A P with R = P^T; sparsified: small
+        # couplings moved to the diagonal (row sums and symmetry kept)
         ref = (Pm.T @ A @ Pm).tocsr()
-        assert abs(Ac - ref).max() <= 1e-12 * abs(ref).max()
+        if drop == 0.0:
+            assert abs(Ac - ref).max() <= 1e-12 * abs(ref).max()
+        else:
+            one = np.ones(ref.shape[0])
+            assert np.max(np.abs(Ac @ one - ref @ one)) <= 1e-12 * abs(ref).max()
+            assert abs(Ac - Ac.T).max() <= 1e-12 * abs(ref).max()
+            d = Ac.diagonal()
+            off = (Ac - sp.diags(d)).tocoo()
+            assert np.all(np.abs(off.data) >= drop * np.sqrt(d[off.row] * d[off.col]) * (1 - 1e-12))
+            assert Ac.nnz <= ref.nnz
         # C points interpolate by injection: some rows are unit vectors
         assert np.isclose(Pm.max(), 1.0) or Pm.max() >= 1.0
         # FSAI: lower triangular, G A G^T has unit diagonal
