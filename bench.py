@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from synth import CONFIGS, gaussian_logk, rhs_uniform  # noqa: E402
+from synth import CONFIGS, batched_problem_specs, gaussian_logk, rhs_uniform  # noqa: E402
 
 METRIC = "AMG-PCG solves/s + SpMM HBM GB/s, 256^3 s=3, mixed vs FP64 at rel-res 1e-8"
 CFG = CONFIGS[3]
@@ -381,6 +381,77 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batched(args):
+    """The batched workload: 64 problems, cube edge N uniform over the even
+    integers in [32, 160], s uniform in {1, 2, 3}, 16 uniform[-1, 1] RHS each,
+    mixed precision to 1e-8, one batched solve per step.  Prints its own JSON
+    line (the default line is the 256^3 workload)."""
+    import torch
+
+    import paper_2407_05930_gb300 as amg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    specs = batched_problem_specs(count=args.batch_count)
+    t0 = time.time()
+    probs, bs = [], []
+    for k, sp in enumerate(specs):
+        P = amg.Problem.structured(sp["N"], 0.0, None, sp["s"]).setup(coarse_max=64)
+        probs.append(P)
+        bs.append(torch.from_numpy(rhs_uniform(P.n, 16, config=4000 + k)).to(dev))
+    t_setup = time.time() - t0
+    B = amg.Batch(probs, [16] * len(probs))
+    kw = dict(tol=1e-8, precision=amg.PREC_MIXED_FP32)
+    xs = [torch.empty_like(b) for b in bs]
+    for _ in range(args.warmup):
+        _, res = B.solve(bs, xs, **kw)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = amg.kernel_launches()
+    torch.cuda.nvtx.range_push("timed_batched")
+    e0.record(st)
+    for _ in range(args.steps):
+        _, res = B.solve(bs, xs, **kw)
+    e1.record(st)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    launches = amg.kernel_launches() - l0
+    nsolves = 16 * len(probs)
+    # FP64 reduced solves of the same problems one at a time (a sample of
+    # `fp64_sample` problems, rate extrapolated by unknowns x RHS)
+    samp = list(range(0, len(probs), max(1, len(probs) // args.fp64_sample)))[: args.fp64_sample]
+    work_all = sum(p.n for p in probs)
+    work_s = sum(probs[i].n for i in samp)
+    for i in samp:
+        probs[i].solve(bs[i], tol=1e-8, precision=amg.PREC_FP64)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for i in samp:
+        probs[i].solve(bs[i], tol=1e-8, precision=amg.PREC_FP64)
+    e1.record(st)
+    torch.cuda.synchronize()
+    sec64 = e0.elapsed_time(e1) * 1e-3 * work_all / work_s
+    line = {
+        "metric": "batched AMG-PCG solves/s (64 problems x 16 RHS, mixed precision, rel-res 1e-8)",
+        "value": nsolves * args.steps / sec, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": CONFIGS[4]["name"], "problems": len(probs),
+                   "cells": int(sum(p.n for p in probs)), "rhs_per_problem": 16,
+                   "sizes": [sp["N"][0] for sp in specs], "s": [sp["s"] for sp in specs]},
+        "inner_iters": res[0].iters, "outer_iters": res[0].outer_iters,
+        "max_relres": float(max(np.max(r.relres) for r in res)), "all_converged": all(r.converged for r in res),
+        "fp64_sequential": {"value": nsolves / sec64, "unit": "solves/s",
+                            "sample": f"{len(samp)} of {len(probs)} problems solved one by one in FP64, "
+                                      "time scaled by unknowns"},
+        "gpu_launches": int(launches), "setup_s": t_setup,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,11 +460,16 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["256cube", "batched"], default="256cube")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--fp64-sample", type=int, default=8)
     ap.add_argument("--profile-only", choices=["mixed", "fp64"], default=None,
                     help="run one marked solve and the roofline SpMM only (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_gpu(args)
 

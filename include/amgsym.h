@@ -292,6 +292,31 @@ amgsym_status amgsym_fv_grad_logk(int32_t d, const int64_t* N, const double* wid
                                   const double* lam_dev, int32_t nrhs, int64_t ld,
                                   double* grad_dev, int32_t accumulate, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched solve (many independent problems in one pass).
+ *
+ * amgsym_batch_create: a batch over `count` problems that are already set up
+ * on one device (amgsym_setup, hierarchies of at least two levels, the same
+ * nu), with nrhs[p] right-hand sides for problem p (nrhs[p] * 2^s_p <= 256).
+ * The batch references the problems; they must outlive it.
+ *
+ * amgsym_batch_solve: solves every problem (Alg. 1 per problem) with the
+ * mixed-precision refinement of amgsym_solve (sopts->precision must be
+ * AMGSYM_PREC_MIXED_FP32 or _BF16).  All problems advance in lock step: each
+ * step of an inner PCG iteration (reduced SpMM, vector updates, every V-cycle
+ * product, coarsest solves) is one persistent work-list launch over all
+ * problems taking part in it, and one iteration is captured in a CUDA graph.
+ * b_dev[p], x_dev[p]: device FP64 natural-order [nrhs[p]][n_p] (leading
+ * dimension n_p).  infos: optional array of `count` records (iters = inner
+ * iterations of the batch, converged and relres per problem).
+ * ---------------------------------------------------------------------- */
+typedef struct amgsym_batch* amgsym_batch_t;
+amgsym_status amgsym_batch_create(const amgsym_t* problems, int32_t count, const int32_t* nrhs,
+                                  amgsym_batch_t* out);
+amgsym_status amgsym_batch_solve(amgsym_batch_t b, const double* const* b_dev, double* const* x_dev,
+                                 const amgsym_solve_opts* sopts, void* stream, amgsym_solve_info* infos);
+void amgsym_batch_destroy(amgsym_batch_t b);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (a replayed CUDA graph counts its kernels).  Host-side counter. */
 int64_t amgsym_kernel_launches(void);

@@ -124,6 +124,10 @@ def _load():
         "amgsym_mirror_perm": (i32, [i32, pi64, i32, pi32]),
         "amgsym_fv_grad_logk": (i32, [i32, pi64, P, P, P, P, i32, i64, P, i32, P]),
         "amgsym_kernel_launches": (i64, []),
+        "amgsym_batch_create": (i32, [ctypes.POINTER(P), i32, pi32, ctypes.POINTER(P)]),
+        "amgsym_batch_solve": (i32, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(SolveOpts), P,
+                                     ctypes.POINTER(SolveInfo)]),
+        "amgsym_batch_destroy": (None, [P]),
         "amgsym_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -144,7 +148,8 @@ EXPORTED = [
         "amgsym_num_levels amgsym_level_sizes amgsym_get_level_matrix amgsym_solve "
         "amgsym_solve_adjoint amgsym_transform_forward amgsym_transform_backward "
         "amgsym_apply_reduced amgsym_vcycle amgsym_vcycle_noalloc amgsym_grid_widths amgsym_fv_nnz "
-        "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy"
+        "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy "
+        "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy"
     ).split()
 ]
 
@@ -394,6 +399,56 @@ class Problem:
         _check(lib.amgsym_vcycle(self._h, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()), nrhs, prec,
                                  1 if finest_hat else 0, self._stream()))
         return Z
+
+
+class Batch:
+    """Many set-up problems solved together (``amgsym_batch_create`` /
+    ``amgsym_batch_solve``): one persistent work-list launch per step of the
+    inner PCG for all problems, one CUDA-graph replay per iteration."""
+
+    def __init__(self, problems, nrhs):
+        self.problems = list(problems)  # keep the problems alive
+        self.nrhs = [int(v) for v in nrhs]
+        if len(self.nrhs) != len(self.problems):
+            raise ValueError("one nrhs per problem")
+        arr = (ctypes.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        nr = np.ascontiguousarray(self.nrhs, dtype=np.int32)
+        self._h = ctypes.c_void_p()
+        _check(lib.amgsym_batch_create(arr, len(self.problems), _ptr(nr, ctypes.c_int32), ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            lib.amgsym_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, bs, xs=None, **kw):
+        """bs: list of CUDA float64 tensors [nrhs_p, n_p]; returns (xs, results)."""
+        import torch
+
+        n = len(self.problems)
+        bs = [b.reshape(self.nrhs[p], self.problems[p].n).contiguous() for p, b in enumerate(bs)]
+        if xs is None:
+            xs = [torch.empty_like(b) for b in bs]
+        kw.setdefault("precision", PREC_MIXED_FP32)
+        o = default_solve_opts(**kw)
+        rel = [np.zeros(self.nrhs[p], dtype=np.float64) for p in range(n)]
+        infos = (SolveInfo * n)()
+        for p in range(n):
+            infos[p].relres = _ptr(rel[p], ctypes.c_double)
+        bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        code = lib.amgsym_batch_solve(self._h, bp, xp, ctypes.byref(o),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), infos)
+        _check(code)
+        res = [SolveResult(infos[p].iters, infos[p].outer_iters, bool(infos[p].converged), rel[p], STATUS[code])
+               for p in range(n)]
+        return xs, res
 
 
 def fv_grad_logk(N, widths_dev, k_dev, u_dev, lam_dev, grad_dev, nrhs: int = 1, accumulate: bool = False):

@@ -167,3 +167,59 @@ int max_grid_blocks();  // blocks for grid-stride kernels (SMs x resident blocks
 int resident_grid(const void* kernel, size_t smem_bytes);
 
 }  // namespace amgsym
+
+namespace amgsym {
+
+// ---------------------------------------------------------------------------
+// Batched (many problems per launch) kernels: k_batch.cu.
+//
+// A batched launch walks a work list of items; an item is a range of rows of
+// one problem's operation (its arguments at index `arg`).  Rows of an item
+// start at a multiple of that problem's row-slot count, so the tile layout of
+// the single-problem kernels applies unchanged.  `slot` numbers the items of
+// one problem (0 .. nslots-1) for the deterministic dot reduction.
+struct BItem {
+  int32_t arg;
+  int32_t first_slot;  // first row slot (row = slot * rows_per_block)
+  int32_t row_end;
+  int32_t slot;
+};
+
+// Where the dot partials of one problem's items go.
+struct BDot {
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  int32_t nslots = 0;
+};
+
+// Arguments of one problem for the batched vector kernels.
+struct UpdArgs {
+  int32_t rows = 0, C = 0;
+  void* x = nullptr;        // update1: x ; update2: p ; copy: dst ; add: y (f64)
+  void* r = nullptr;        // update1: r
+  const void* p = nullptr;  // update1: p ; update2: z ; copy/add: src
+  const void* q = nullptr;  // update1: q
+  const double* beta = nullptr;
+  const int32_t* skip = nullptr;
+  DotArgs dot;
+};
+
+// Dense coarsest-level solve of one problem.
+struct CoarseArgs {
+  int32_t n = 0, C = 0;
+  const double* Ainv = nullptr;
+  const void* Y = nullptr;
+  void* Z = nullptr;
+  const int32_t* skip = nullptr;
+};
+
+enum BatchVecOp { BOP_UPDATE1 = 0, BOP_UPDATE2 = 1, BOP_COPY = 2 };
+
+void launch_spmm_batch(ValType mt, VecType xt, VecType ot, int cpt, int kl, bool dot, bool iface,
+                       const SpmmArgs* args, const BItem* items, int32_t n_items, const BDot* dots,
+                       size_t smem, cudaStream_t st);
+void launch_vec_batch(int op, VecType vt, int cpt, const UpdArgs* args, const BItem* items, int32_t n_items,
+                      const BDot* dots, size_t smem, cudaStream_t st);
+void launch_coarse_batch(VecType vt, const CoarseArgs* args, const BItem* items, int32_t n_items, cudaStream_t st);
+
+}  // namespace amgsym

@@ -97,7 +97,8 @@ __host__ __device__ inline int dot_smem_doubles(int S, int rows_pb, int C) {
 
 template <int CPT>
 __device__ __forceinline__ void block_dot(const DotArgs& d, double (&part)[CPT], int c0, bool has_cols,
-                                          int rloc, int rows_pb, int S, int C, double* sm) {
+                                          int rloc, int rows_pb, int S, int C, double* sm, int slot, int nslots,
+                                          double* partials, unsigned* ticket) {
   const bool pow2 = (S & (S - 1)) == 0 && S <= 32;
   int lines;
   if (pow2) {
@@ -136,27 +137,27 @@ __device__ __forceinline__ void block_dot(const DotArgs& d, double (&part)[CPT],
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
     double t = 0.0;
     for (int sl = 0; sl < slices; ++sl) t += red[sl * C + c];
-    d.sc.partials[(int64_t)blockIdx.x * C + c] = t;
+    partials[(int64_t)slot * C + c] = t;
   }
   __threadfence();
   __syncthreads();
   __shared__ unsigned is_last;
-  if (threadIdx.x == 0) is_last = (atomicAdd(d.sc.ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == (unsigned)nslots - 1u) ? 1u : 0u;
   __syncthreads();
   if (!is_last) return;
   __threadfence();
   if ((int)threadIdx.x < slices * C) {
     const int c = threadIdx.x % C, sl = threadIdx.x / C;
-    const int nblk = (int)gridDim.x;
+    const int nblk = nslots;
     double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
     int b = sl;
     for (; b + 3 * slices < nblk; b += 4 * slices) {
-      t0 += __ldcg(d.sc.partials + (int64_t)b * C + c);
-      t1 += __ldcg(d.sc.partials + (int64_t)(b + slices) * C + c);
-      t2 += __ldcg(d.sc.partials + (int64_t)(b + 2 * slices) * C + c);
-      t3 += __ldcg(d.sc.partials + (int64_t)(b + 3 * slices) * C + c);
+      t0 += __ldcg(partials + (int64_t)b * C + c);
+      t1 += __ldcg(partials + (int64_t)(b + slices) * C + c);
+      t2 += __ldcg(partials + (int64_t)(b + 2 * slices) * C + c);
+      t3 += __ldcg(partials + (int64_t)(b + 3 * slices) * C + c);
     }
-    for (; b < nblk; b += slices) t0 += __ldcg(d.sc.partials + (int64_t)b * C + c);
+    for (; b < nblk; b += slices) t0 += __ldcg(partials + (int64_t)b * C + c);
     red[sl * C + c] = (t0 + t1) + (t2 + t3);
   }
   __syncthreads();
@@ -169,7 +170,8 @@ __device__ __forceinline__ void block_dot(const DotArgs& d, double (&part)[CPT],
   }
   __syncthreads();
   dot_finalize_rhs(d, colsum);
-  if (threadIdx.x == 0) *d.sc.ticket = 0u;
+  if (threadIdx.x == 0) *ticket = 0u;
+  __syncthreads();  // the block may go on to reuse the shared scratch
 }
 
 }  // namespace amgsym

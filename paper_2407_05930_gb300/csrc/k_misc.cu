@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(kBlock) cg_update1_kernel(int64_t rows, int32_
     double pd[CPT];
 #pragma unroll
     for (int k = 0; k < CPT; ++k) pd[k] = has_cols ? (double)part[k] : 0.0;
-    block_dot<CPT>(dot, pd, c0, has_cols, rloc, rows_pb, TPR, C, sm);
+    block_dot<CPT>(dot, pd, c0, has_cols, rloc, rows_pb, TPR, C, sm, blockIdx.x, gridDim.x, dot.sc.partials,
+                   dot.sc.ticket);
   }
 }
 
@@ -374,7 +375,8 @@ __global__ void __launch_bounds__(kBlock) dot_kernel(int64_t rows, int32_t C, co
     for (int64_t row = blockIdx.x * (int64_t)rows_pb + rloc; row < rows; row += (int64_t)gridDim.x * rows_pb)
       part[0] += (double)a[row * C + c0] * (double)b[row * C + c0];
   extern __shared__ double sm[];
-  block_dot<1>(dot, part, c0, has_cols, rloc, rows_pb, TPR, C, sm);
+  block_dot<1>(dot, part, c0, has_cols, rloc, rows_pb, TPR, C, sm, blockIdx.x, gridDim.x, dot.sc.partials,
+               dot.sc.ticket);
 }
 
 void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,

@@ -21,206 +21,29 @@
 // an optional per-column dot (W.Y or Y.Y) reduced deterministically.
 #include <cuda_bf16.h>
 
-#include "device.h"
-#include "dot.cuh"
+#include "spmm_common.cuh"
 
 namespace amgsym {
 
-template <typename T>
-struct AccOf {
-  using type = float;
-};
-template <>
-struct AccOf<double> {
-  using type = double;
-};
-
-template <typename T>
-__device__ __forceinline__ float to_f(T v) {
-  return (float)v;
-}
-template <>
-__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
-  return __bfloat162float(v);
-}
-
-template <typename A, typename T>
-__device__ __forceinline__ A cvt(T v) {
-  return (A)v;
-}
-template <>
-__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 v) {
-  return __bfloat162float(v);
-}
-template <>
-__device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 v) {
-  return (double)__bfloat162float(v);
-}
-
-// Vector of N consecutive T, aligned to its size up to 32 bytes (a 32-byte
-// vector is one 256-bit access where the hardware has it, else two 16-byte ones).
-template <typename T, int N>
-struct alignas(sizeof(T) * N <= 32 ? sizeof(T) * N : 32) Vec {
-  T v[N];
-};
-
-template <typename T, int N>
-__device__ __forceinline__ Vec<T, N> ldv(const T* p) {
-  return *reinterpret_cast<const Vec<T, N>*>(p);
-}
-template <typename T, int N>
-__device__ __forceinline__ Vec<T, N> ldv_stream(const T* p) {
-  return __ldcs(reinterpret_cast<const Vec<T, N>*>(p));
-}
-template <typename T, int N>
-__device__ __forceinline__ void stv(T* p, const Vec<T, N>& v) {
-  *reinterpret_cast<Vec<T, N>*>(p) = v;
-}
-
-// The compute type: FP64 if either operand is FP64, else FP32.
-template <typename MT, typename XT>
-struct ComputeOf {
-  using type = float;
-};
-template <typename XT>
-struct ComputeOf<double, XT> {
-  using type = double;
-};
-template <typename MT>
-struct ComputeOf<MT, double> {
-  using type = double;
-};
-template <>
-struct ComputeOf<double, double> {
-  using type = double;
-};
-
-// Thread layout.  A row is served by S = TPC * KL threads: TPC column
-// threads (each owning CPT consecutive columns, TPC = C / CPT) times KL entry
-// lanes (lane e takes the row's entries e, e + KL, ...).  The KL partial sums
-// are combined with warp shuffles (S divides 32 when KL > 1), and entry lane 0
-// runs the epilogue.  KL > 1 keeps several gathers of one row in flight, which
-// is what hides the ptr -> idx -> X latency chain of short rows and spreads the
-// long rows of the coarse levels over many lanes.
 template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE>
-__global__ void __launch_bounds__(kBlock, 8) spmm_kernel(SpmmArgs a) {
-  using CT = typename ComputeOf<MT, XT>::type;
-  using DT = typename AccOf<XT>::type;  // per-thread dot partial type
-  if (a.skip && *a.skip == 0) return;   // uniform over the grid
-  const int C = a.C;
-  const int TPC = C / CPT;
-  const int S = TPC * KL;
-  const int rows_pb = kBlock / S;
-  const int g = threadIdx.x / S;
-  const int w = threadIdx.x - g * S;
-  const int e = KL > 1 ? w / TPC : 0;
-  const int c0 = (w - e * TPC) * CPT;
-  const bool slot_ok = g < rows_pb;
-  const MT* __restrict__ val = static_cast<const MT*>(a.val);
-  const XT* __restrict__ X = static_cast<const XT*>(a.X);
-  // Y may alias Z (in-place update z += ...); each row reads Z before writing Y.
-  const XT* Z = static_cast<const XT*>(a.Z);
-  OT* Y = static_cast<OT*>(a.Y);
-  const int32_t* __restrict__ ptr = a.ptr;
-  const int32_t* __restrict__ idx = a.idx;
-  const CT alpha = (CT)a.alpha, beta = (CT)a.beta;
+__global__ void __launch_bounds__(kBlock, (CPT >= 8 ? 4 : 8)) spmm_kernel(SpmmArgs a) {
+  using DT = typename AccOf<XT>::type;
+  if (a.skip && *a.skip == 0) return;  // uniform over the grid
   DT dpart[CPT];
 #pragma unroll
   for (int q = 0; q < CPT; ++q) dpart[q] = (DT)0;
-
   // Grid-stride over row slots: a wave of blocks sweeps one contiguous window
   // of rows, so the far neighbours one block gathers were recently brought
-  // into L2 by another.  The trip count is block-uniform (the shuffles need
-  // every lane of the warp).
-  for (int base = blockIdx.x * rows_pb; base < a.rows; base += gridDim.x * rows_pb) {
-    const int row = base + g;
-    const bool live = slot_ok && row < a.rows;
-    CT acc[CPT];
-#pragma unroll
-    for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
-    if (live) {
-      const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
-      int k = kb + e;
-      for (; k + KL < ke; k += 2 * KL) {
-        const int j0 = __ldg(idx + k), j1 = __ldg(idx + k + KL);
-        const CT m0 = cvt<CT>(val[k]), m1 = cvt<CT>(val[k + KL]);
-        const Vec<XT, CPT> x0 = ldv<XT, CPT>(X + (int64_t)j0 * C + c0);
-        const Vec<XT, CPT> x1 = ldv<XT, CPT>(X + (int64_t)j1 * C + c0);
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-          acc[q] = fma(m0, (CT)x0.v[q], acc[q]);
-          acc[q] = fma(m1, (CT)x1.v[q], acc[q]);
-        }
-      }
-      if (k < ke) {
-        const int j0 = __ldg(idx + k);
-        const CT m0 = cvt<CT>(val[k]);
-        const Vec<XT, CPT> x0 = ldv<XT, CPT>(X + (int64_t)j0 * C + c0);
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) acc[q] = fma(m0, (CT)x0.v[q], acc[q]);
-      }
-      if (HAS_IFACE && e == 0) {
-        const uint32_t wd = __ldg(a.imask + (row >> 5));
-        const uint32_t bit = 1u << (row & 31);
-        if (wd & bit) {
-          const int f = __ldg(a.iprefix + (row >> 5)) + __popc(wd & (bit - 1u));
-          const CT* __restrict__ iv = static_cast<const CT*>(a.ival);
-          for (int ee = __ldg(a.iptr + f); ee < __ldg(a.iptr + f + 1); ++ee) {
-            const int j = __ldg(a.icol + ee);
-            const Vec<XT, CPT> xv = ldv<XT, CPT>(X + (int64_t)j * C + c0);
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-              const int blk = (c0 + q) % a.nb;
-              acc[q] = fma(iv[(int64_t)ee * a.nb + blk], (CT)xv.v[q], acc[q]);
-            }
-          }
-        }
-      }
-    }
-    if (KL > 1) {
-#pragma unroll
-      for (int off = KL / 2; off >= 1; off >>= 1) {
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off * TPC);
-      }
-    }
-    if (live && e == 0) {
-      Vec<OT, CPT> out;
-      if (a.beta != 0.0) {
-        const Vec<XT, CPT> zv = ldv<XT, CPT>(Z + (int64_t)row * C + c0);
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-          const CT y = alpha * acc[q] + beta * (CT)zv.v[q];
-          out.v[q] = (OT)y;
-          acc[q] = y;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-          const CT y = alpha * acc[q];
-          out.v[q] = (OT)y;
-          acc[q] = y;
-        }
-      }
-      stv<OT, CPT>(Y + (int64_t)row * C + c0, out);
-      if (HAS_DOT) {
-        if (a.dot.mode == DOT_WY) {
-          const Vec<XT, CPT> wv = ldv<XT, CPT>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
-#pragma unroll
-          for (int q = 0; q < CPT; ++q) dpart[q] += (DT)wv.v[q] * (DT)acc[q];
-        } else {
-#pragma unroll
-          for (int q = 0; q < CPT; ++q) dpart[q] += (DT)acc[q] * (DT)acc[q];
-        }
-      }
-    }
-  }
+  // into L2 by another.
+  spmm_tile<MT, XT, OT, CPT, KL, HAS_DOT, HAS_IFACE>(a, blockIdx.x, gridDim.x, a.rows, dpart);
   if (HAS_DOT) {
+    const TileLayout t = tile_layout<CPT, KL>(a.C);
     extern __shared__ double sm[];
     double part[CPT];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) part[q] = (slot_ok && e == 0) ? (double)dpart[q] : 0.0;
-    block_dot<CPT>(a.dot, part, c0, slot_ok && e == 0, g, rows_pb, S, C, sm);
+    for (int q = 0; q < CPT; ++q) part[q] = (t.slot_ok && t.e == 0) ? (double)dpart[q] : 0.0;
+    block_dot<CPT>(a.dot, part, t.c0, t.slot_ok && t.e == 0, t.g, t.rows_pb, t.S, a.C, sm, blockIdx.x,
+                   gridDim.x, a.dot.sc.partials, a.dot.sc.ticket);
   }
 }
 

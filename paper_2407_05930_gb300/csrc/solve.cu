@@ -19,82 +19,14 @@
 
 #include "device.h"
 #include "internal.h"
+#include "solver.h"
 
 namespace amgsym {
 
-#define CK(call)                                                                          \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
-      fail(e_ == cudaErrorMemoryAllocation ? AMGSYM_ERR_OOM : AMGSYM_ERR_CUDA,            \
-           std::string(#call) + ": " + cudaGetErrorString(e_));                          \
-  } while (0)
-
-static void check_launch() {
+void check_launch() {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) fail(AMGSYM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
 }
-
-// Precision-specific work arrays for one column count.
-struct LevelWork {
-  void* y = nullptr;  // level rhs (levels >= 1)
-  void* z = nullptr;  // level solution (levels >= 1)
-  void* r = nullptr;  // residual
-  void* t = nullptr;  // smoother temporary
-};
-
-struct PrecWork {
-  bool ready = false;
-  std::vector<LevelWork> lw;
-  void *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;  // PCG vectors
-};
-
-struct GraphKey {
-  int mode = -1;
-  int32_t nrhs = 0;
-  double tol = 0.0;
-  bool operator==(const GraphKey& o) const { return mode == o.mode && nrhs == o.nrhs && tol == o.tol; }
-};
-
-struct GraphCache {
-  cudaGraphExec_t exec = nullptr;
-  GraphKey key;
-};
-
-// SpMM tile (columns per thread, entry lanes per row) chosen by the tuner for
-// one matrix, column count and precision combination.
-struct Tile {
-  int cpt = 0, kl = 0;
-};
-using TileKey = std::tuple<const void*, int32_t, int, int, int>;  // matrix idx array, C, mt, xt, ot
-
-struct Device {
-  int device_id = 0;
-  std::map<TileKey, Tile> tiles;
-  std::set<std::tuple<int32_t, int, int>> tuned;  // (C, vt, mt) already tuned
-  int precisions = 3;
-  int nu = 1;
-  int32_t s = 0, nb = 1;
-  int64_t n_b = 0;
-  DevCsr Ainn;  // alias of lv[0].A
-  DevIface iface;
-  int32_t* perm = nullptr;
-  std::vector<DevLevel> lv;
-  std::vector<void*> owned;  // setup allocations
-  // work arrays for work_nrhs right-hand sides
-  int32_t work_nrhs = 0;
-  std::vector<void*> work_owned;
-  double* bh = nullptr;  // b^ (FP64)
-  double* xh = nullptr;  // x^ (FP64)
-  PrecWork w64, w32;
-  DevScalars sc_out, sc_in;
-  int32_t* h_status = nullptr;  // pinned [2][4]
-  double* h_relres = nullptr;   // pinned [work_nrhs]
-  cudaStream_t cap_stream = nullptr;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  GraphCache graph;
-  int64_t graph_kernels = 0;
-};
 
 template <typename T>
 static T* dalloc(std::vector<void*>& owner, int64_t count) {
@@ -229,7 +161,7 @@ void device_upload(amgsym_problem* p) {
   CK(cudaDeviceSynchronize());
 }
 
-static void alloc_scalars(Device* D, DevScalars& sc, int32_t C, int32_t nrhs) {
+void alloc_scalars(Device* D, DevScalars& sc, int32_t C, int32_t nrhs) {
   sc.rz = dalloc<double>(D->work_owned, C);
   sc.alpha = dalloc<double>(D->work_owned, C);
   sc.beta = dalloc<double>(D->work_owned, C);
@@ -246,10 +178,11 @@ static void alloc_scalars(Device* D, DevScalars& sc, int32_t C, int32_t nrhs) {
   CK(cudaMemset(sc.status, 0, 4 * sizeof(int32_t)));
 }
 
-static void ensure_work(Device* D, int32_t nrhs, VecType vt) {
+void ensure_work(Device* D, int32_t nrhs, VecType vt) {
   if (nrhs > D->work_nrhs) {
     CK(cudaDeviceSynchronize());
     free_work(D);
+    D->work_gen++;
     D->work_nrhs = nrhs;
     const int32_t C = nrhs * D->nb;
     D->bh = dalloc<double>(D->work_owned, D->n_b * C);
@@ -261,6 +194,7 @@ static void ensure_work(Device* D, int32_t nrhs, VecType vt) {
   }
   PrecWork& W = vt == VEC_F64 ? D->w64 : D->w32;
   if (W.ready) return;
+  D->work_gen++;
   const int32_t C = D->work_nrhs * D->nb;
   const size_t es = vt == VEC_F64 ? 8 : 4;
   auto vec = [&](int64_t rows) -> void* {
@@ -292,22 +226,11 @@ static void ensure_work(Device* D, int32_t nrhs, VecType vt) {
 // ---------------------------------------------------------------------------
 // Kernel sequencing.
 
-struct Ctx {
-  Device* D;
-  int32_t C;
-  VecType vt;       // vector precision of the V-cycle / inner PCG
-  ValType mt;       // matrix value precision of the V-cycle
-  bool finest_hat;  // V-cycle level-0 residual with A^_i
-  cudaStream_t st;
-  const int32_t* skip = nullptr;  // early-exit flag (active RHS count) of the PCG loop
-  bool tune = false;              // run the tile autotuner before the first PCG loop
-};
-
 // Entry lanes per row: one lane for short rows (fine-level stencils, where
 // the L1-resident neighbours keep the gathers cheap), then about 5 entries per
 // lane for the longer rows of the coarse Galerkin operators, at most 32
 // threads per row.
-static int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt) {
+int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt) {
   const int cpt = xt == VEC_F64 ? 2 : 4;
   const int tpc = (C % cpt == 0) ? C / cpt : C;
   int kl = 1;
@@ -315,8 +238,8 @@ static int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt) {
   return kl;
 }
 
-static void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X, void* Y,
-                 double alpha, double beta, const void* Z, bool iface, const DotArgs* dot) {
+SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X,
+                        void* Y, double alpha, double beta, const void* Z, bool iface, const DotArgs* dot) {
   SpmmArgs a;
   a.rows = M.rows;
   a.C = c.C;
@@ -347,6 +270,12 @@ static void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType 
   } else {
     a.kl = entry_lanes(M, c.C, xt);
   }
+  return a;
+}
+
+void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X, void* Y, double alpha,
+          double beta, const void* Z, bool iface, const DotArgs* dot) {
+  const SpmmArgs a = make_spmm_args(c, M, mt, xt, ot, X, Y, alpha, beta, Z, iface, dot);
   launch_spmm(mt, xt, ot, a, c.st);
   check_launch();
 }
@@ -359,7 +288,7 @@ static void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType 
 // runs once per (C, precision) before the PCG graph is captured, on scratch
 // level vectors (their contents do not matter for timing).  Results are
 // bit-reproducible for a fixed tile choice; the choice itself is timing-based.
-static void tune_tiles(const Ctx& c) {
+void tune_tiles(const Ctx& c) {
   Device* D = c.D;
   auto key = std::make_tuple(c.C, (int)c.vt, (int)c.mt);
   if (D->tuned.count(key)) return;
@@ -473,7 +402,7 @@ static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* l
   }
 }
 
-static DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb,
+DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb,
                         double /*tol: the device scalar sc.tol2 holds it*/, int count_iter) {
   DotArgs d;
   d.mode = mode;
@@ -502,7 +431,7 @@ static void pcg_iteration(const Ctx& c, PrecWork& W, const DevScalars& sc, int32
   check_launch();
 }
 
-static void read_status(Device* D, const DevScalars& sc, cudaStream_t st, int32_t* out4) {
+void read_status(Device* D, const DevScalars& sc, cudaStream_t st, int32_t* out4) {
   CK(cudaMemcpyAsync(D->h_status, sc.status, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   std::memcpy(out4, D->h_status, 4 * sizeof(int32_t));
@@ -587,12 +516,12 @@ static int pcg_loop(const Ctx& c0, PrecWork& W, const DevScalars& sc, int32_t nr
   return done_at < 0 ? maxit : done_at;
 }
 
-static void check_ptr(const void* p, const char* what) {
+void check_ptr(const void* p, const char* what) {
   if (!p) fail(AMGSYM_ERR_ARG, std::string(what) + " is NULL");
   if (((uintptr_t)p) % 16) fail(AMGSYM_ERR_ARG, std::string(what) + " must be 16-byte aligned");
 }
 
-static Device* require_dev(amgsym_t h) {
+Device* require_dev(amgsym_t h) {
   if (!h) fail(AMGSYM_ERR_ARG, "NULL handle");
   if (!h->dev) fail(AMGSYM_ERR_STATE, "problem is not on the device (call amgsym_setup without host_only)");
   CK(cudaSetDevice(h->dev->device_id));

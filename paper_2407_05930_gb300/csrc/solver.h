@@ -1,0 +1,115 @@
+// Host-side state of a problem on the device and the sequencing helpers
+// shared by the single-problem solve (solve.cu) and the batched solve
+// (batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "device.h"
+#include "internal.h"
+
+namespace amgsym {
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      fail(e_ == cudaErrorMemoryAllocation ? AMGSYM_ERR_OOM : AMGSYM_ERR_CUDA,            \
+           std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+void check_launch();
+
+// Precision-specific work arrays for one column count.
+struct LevelWork {
+  void* y = nullptr;  // level rhs (levels >= 1)
+  void* z = nullptr;  // level solution (levels >= 1)
+  void* r = nullptr;  // residual
+  void* t = nullptr;  // smoother temporary
+};
+
+struct PrecWork {
+  bool ready = false;
+  std::vector<LevelWork> lw;
+  void *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;  // PCG vectors
+};
+
+struct GraphKey {
+  int mode = -1;
+  int32_t nrhs = 0;
+  double tol = 0.0;
+  bool operator==(const GraphKey& o) const { return mode == o.mode && nrhs == o.nrhs && tol == o.tol; }
+};
+
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key;
+};
+
+// SpMM tile (columns per thread, entry lanes per row) chosen by the tuner for
+// one matrix, column count and precision combination.
+struct Tile {
+  int cpt = 0, kl = 0;
+};
+using TileKey = std::tuple<const void*, int32_t, int, int, int>;  // matrix idx array, C, mt, xt, ot
+
+struct Device {
+  int device_id = 0;
+  uint64_t work_gen = 0;  // bumped whenever work arrays are (re)allocated
+  std::map<TileKey, Tile> tiles;
+  std::set<std::tuple<int32_t, int, int>> tuned;  // (C, vt, mt) already tuned
+  int precisions = 3;
+  int nu = 1;
+  int32_t s = 0, nb = 1;
+  int64_t n_b = 0;
+  DevCsr Ainn;  // alias of lv[0].A
+  DevIface iface;
+  int32_t* perm = nullptr;
+  std::vector<DevLevel> lv;
+  std::vector<void*> owned;  // setup allocations
+  // work arrays for work_nrhs right-hand sides
+  int32_t work_nrhs = 0;
+  std::vector<void*> work_owned;
+  double* bh = nullptr;  // b^ (FP64)
+  double* xh = nullptr;  // x^ (FP64)
+  PrecWork w64, w32;
+  DevScalars sc_out, sc_in;
+  int32_t* h_status = nullptr;  // pinned [2][4]
+  double* h_relres = nullptr;   // pinned [work_nrhs]
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  GraphCache graph;
+  int64_t graph_kernels = 0;
+};
+
+struct Ctx {
+  Device* D;
+  int32_t C;
+  VecType vt;       // vector precision of the V-cycle / inner PCG
+  ValType mt;       // matrix value precision of the V-cycle
+  bool finest_hat;  // V-cycle level-0 residual with A^_i
+  cudaStream_t st;
+  const int32_t* skip = nullptr;  // early-exit flag (active RHS count) of the PCG loop
+  bool tune = false;              // run the tile autotuner before the first PCG loop
+};
+
+
+void ensure_work(Device* D, int32_t nrhs, VecType vt);
+void tune_tiles(const Ctx& c);
+int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt);
+SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X,
+                        void* Y, double alpha, double beta, const void* Z, bool iface, const DotArgs* dot);
+void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X, void* Y, double alpha,
+          double beta, const void* Z, bool iface, const DotArgs* dot);
+DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb, double tol,
+                 int count_iter);
+Device* require_dev(amgsym_t h);
+void check_ptr(const void* p, const char* what);
+
+}  // namespace amgsym

@@ -1,0 +1,227 @@
+// Device code shared by the single-problem and batched SpMM kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "device.h"
+#include "dot.cuh"
+
+namespace amgsym {
+
+template <typename T>
+struct AccOf {
+  using type = float;
+};
+template <>
+struct AccOf<double> {
+  using type = double;
+};
+
+template <typename T>
+__device__ __forceinline__ float to_f(T v) {
+  return (float)v;
+}
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
+template <typename A, typename T>
+__device__ __forceinline__ A cvt(T v) {
+  return (A)v;
+}
+template <>
+__device__ __forceinline__ float cvt<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ double cvt<double, __nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+
+// Vector of N consecutive T, aligned to its size up to 32 bytes (a 32-byte
+// vector is one 256-bit access where the hardware has it, else two 16-byte ones).
+template <typename T, int N>
+struct alignas(sizeof(T) * N <= 32 ? sizeof(T) * N : 32) Vec {
+  T v[N];
+};
+
+template <typename T, int N>
+__device__ __forceinline__ Vec<T, N> ldv(const T* p) {
+  return *reinterpret_cast<const Vec<T, N>*>(p);
+}
+template <typename T, int N>
+__device__ __forceinline__ Vec<T, N> ldv_stream(const T* p) {
+  return __ldcs(reinterpret_cast<const Vec<T, N>*>(p));
+}
+template <typename T, int N>
+__device__ __forceinline__ void stv(T* p, const Vec<T, N>& v) {
+  *reinterpret_cast<Vec<T, N>*>(p) = v;
+}
+
+// The compute type: FP64 if either operand is FP64, else FP32.
+template <typename MT, typename XT>
+struct ComputeOf {
+  using type = float;
+};
+template <typename XT>
+struct ComputeOf<double, XT> {
+  using type = double;
+};
+template <typename MT>
+struct ComputeOf<MT, double> {
+  using type = double;
+};
+template <>
+struct ComputeOf<double, double> {
+  using type = double;
+};
+
+// Rows [first_slot * rows_pb + k * slot_step * rows_pb, ...) below row_end
+// of one SpMM, for the whole block; this thread's dot partial (entry lane 0
+// only) is added to dpart.  Thread layout: a row is served by S = TPC * KL
+// threads: TPC column threads (each owning CPT consecutive columns, TPC =
+// C / CPT) times KL entry lanes (lane e takes the row's entries e, e + KL,
+// ...).  The KL partial sums are combined with warp shuffles (S divides 32
+// when KL > 1), and entry lane 0 runs the epilogue.  KL > 1 keeps several
+// gathers of one row in flight (the ptr -> idx -> X latency chain) and spreads
+// the long rows of the coarse levels over many lanes.
+template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE>
+__device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int slot_step, int row_end,
+                                          typename AccOf<XT>::type (&dpart)[CPT]) {
+  using CT = typename ComputeOf<MT, XT>::type;
+  using DT = typename AccOf<XT>::type;  // per-thread dot partial type
+  const int C = a.C;
+  const int TPC = C / CPT;
+  const int S = TPC * KL;
+  const int rows_pb = kBlock / S;
+  const int g = threadIdx.x / S;
+  const int w = threadIdx.x - g * S;
+  const int e = KL > 1 ? w / TPC : 0;
+  const int c0 = (w - e * TPC) * CPT;
+  const bool slot_ok = g < rows_pb;
+  const MT* __restrict__ val = static_cast<const MT*>(a.val);
+  const XT* __restrict__ X = static_cast<const XT*>(a.X);
+  // Y may alias Z (in-place update z += ...); each row reads Z before writing Y.
+  const XT* Z = static_cast<const XT*>(a.Z);
+  OT* Y = static_cast<OT*>(a.Y);
+  const int32_t* __restrict__ ptr = a.ptr;
+  const int32_t* __restrict__ idx = a.idx;
+  const CT alpha = (CT)a.alpha, beta = (CT)a.beta;
+
+  // The trip count is block-uniform (the shuffles need every lane of the warp).
+  for (int base = first_slot * rows_pb; base < row_end; base += slot_step * rows_pb) {
+    const int row = base + g;
+    const bool live = slot_ok && row < row_end;
+    CT acc[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
+    if (live) {
+      const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
+      int k = kb + e;
+      // U entries per step: all index/value loads first, then all gathers,
+      // so U gathers of this lane are in flight at once
+      constexpr int U = CPT >= 8 ? 2 : 4;
+      for (; k + (U - 1) * KL < ke; k += U * KL) {
+        int j[U];
+        CT m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          j[u] = __ldg(idx + k + u * KL);
+          m[u] = cvt<CT>(val[k + u * KL]);
+        }
+        Vec<XT, CPT> x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = ldv<XT, CPT>(X + (int64_t)j[u] * C + c0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+#pragma unroll
+          for (int q = 0; q < CPT; ++q) acc[q] = fma(m[u], (CT)x[u].v[q], acc[q]);
+        }
+      }
+      for (; k < ke; k += KL) {
+        const int j0 = __ldg(idx + k);
+        const CT m0 = cvt<CT>(val[k]);
+        const Vec<XT, CPT> x0 = ldv<XT, CPT>(X + (int64_t)j0 * C + c0);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) acc[q] = fma(m0, (CT)x0.v[q], acc[q]);
+      }
+      if (HAS_IFACE && e == 0) {
+        const uint32_t wd = __ldg(a.imask + (row >> 5));
+        const uint32_t bit = 1u << (row & 31);
+        if (wd & bit) {
+          const int f = __ldg(a.iprefix + (row >> 5)) + __popc(wd & (bit - 1u));
+          const CT* __restrict__ iv = static_cast<const CT*>(a.ival);
+          for (int ee = __ldg(a.iptr + f); ee < __ldg(a.iptr + f + 1); ++ee) {
+            const int j = __ldg(a.icol + ee);
+            const Vec<XT, CPT> xv = ldv<XT, CPT>(X + (int64_t)j * C + c0);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+              const int blk = (c0 + q) % a.nb;
+              acc[q] = fma(iv[(int64_t)ee * a.nb + blk], (CT)xv.v[q], acc[q]);
+            }
+          }
+        }
+      }
+    }
+    if (KL > 1) {
+#pragma unroll
+      for (int off = KL / 2; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off * TPC);
+      }
+    }
+    if (live && e == 0) {
+      Vec<OT, CPT> out;
+      if (a.beta != 0.0) {
+        const Vec<XT, CPT> zv = ldv<XT, CPT>(Z + (int64_t)row * C + c0);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+          const CT y = alpha * acc[q] + beta * (CT)zv.v[q];
+          out.v[q] = (OT)y;
+          acc[q] = y;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+          const CT y = alpha * acc[q];
+          out.v[q] = (OT)y;
+          acc[q] = y;
+        }
+      }
+      stv<OT, CPT>(Y + (int64_t)row * C + c0, out);
+      if (HAS_DOT) {
+        if (a.dot.mode == DOT_WY) {
+          const Vec<XT, CPT> wv = ldv<XT, CPT>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
+#pragma unroll
+          for (int q = 0; q < CPT; ++q) dpart[q] += (DT)wv.v[q] * (DT)acc[q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < CPT; ++q) dpart[q] += (DT)acc[q] * (DT)acc[q];
+        }
+      }
+    }
+  }
+}
+
+// The thread's place in the tile layout (see spmm_tile).
+struct TileLayout {
+  int S, rows_pb, g, e, c0;
+  bool slot_ok;
+};
+
+template <int CPT, int KL>
+__device__ __forceinline__ TileLayout tile_layout(int C) {
+  TileLayout t;
+  const int TPC = C / CPT;
+  t.S = TPC * KL;
+  t.rows_pb = kBlock / t.S;
+  t.g = threadIdx.x / t.S;
+  const int w = threadIdx.x - t.g * t.S;
+  t.e = KL > 1 ? w / TPC : 0;
+  t.c0 = (w - t.e * TPC) * CPT;
+  t.slot_ok = t.g < t.rows_pb;
+  return t;
+}
+
+}  // namespace amgsym
