@@ -81,6 +81,27 @@ static T* bupload(std::vector<void*>& owner, const std::vector<T>& v) {
   return static_cast<T*>(p);
 }
 
+// Dot scratch of one (launch, problem): partials, chunk partials and zeroed
+// tickets for the two-level reduction of block_dot2.
+static BDot alloc_bdot(Batch* B, int32_t nslots, int32_t C) {
+  BDot bd;
+  const int32_t nch = (nslots + 31) / 32;
+  void* p = nullptr;
+  BCK(cudaMalloc(&p, sizeof(double) * (size_t)nslots * C));
+  B->plan_owned.push_back(p);
+  bd.partials = static_cast<double*>(p);
+  BCK(cudaMalloc(&p, sizeof(double) * (size_t)nch * C));
+  B->plan_owned.push_back(p);
+  bd.chunk_partials = static_cast<double*>(p);
+  BCK(cudaMalloc(&p, sizeof(unsigned) * (size_t)(nch + 1)));
+  B->plan_owned.push_back(p);
+  BCK(cudaMemset(p, 0, sizeof(unsigned) * (size_t)(nch + 1)));
+  bd.chunk_tickets = static_cast<unsigned*>(p);
+  bd.ticket = bd.chunk_tickets + nch;
+  bd.nslots = nslots;
+  return bd;
+}
+
 static void free_plans(Batch* B) {
   for (void* p : B->plan_owned) cudaFree(p);
   B->plan_owned.clear();
@@ -92,24 +113,15 @@ static void free_plans(Batch* B) {
   B->planned_key = -1;
 }
 
-// Rows per item (in row slots of rows_pb rows).  Items without a fused dot
-// are sized so that one wave of resident blocks touches about 48 MB of the
-// gathered vector (row_bytes per row): the far-neighbour rows a block gathers
-// are then still in L2 from the blocks working just behind it, even when the
-// vector is larger than L2.  Items with a fused dot are at most 1024 per
-// problem (one partial per item).
-static int slots_per_item(int64_t rows, int rows_pb, bool dot, int64_t row_bytes) {
-  const int64_t slots = (rows + rows_pb - 1) / rows_pb;
-  int64_t m;
-  if (dot) {
-    m = std::max<int64_t>(1, 1024 / rows_pb);
-    if ((slots + m - 1) / m > 1024) m = (slots + 1023) / 1024;
-  } else {
-    const int64_t wave = (int64_t)max_grid_blocks();
-    const int64_t rows_item = std::max<int64_t>(rows_pb, (int64_t(48) << 20) / (wave * std::max<int64_t>(row_bytes, 1)));
-    m = std::max<int64_t>(1, std::min<int64_t>(rows_item / rows_pb, 4096 / rows_pb));
-  }
-  return (int)m;
+// Rows per item (in row slots of rows_pb rows): sized so that one wave of
+// resident blocks touches about 48 MB of the gathered vector (row_bytes per
+// row).  The far-neighbour rows a block gathers are then still in L2 from the
+// blocks working just behind it, even when the vector is larger than L2.
+static int slots_per_item(int64_t rows, int rows_pb, int64_t row_bytes) {
+  (void)rows;
+  const int64_t wave = (int64_t)max_grid_blocks();
+  const int64_t rows_item = std::max<int64_t>(rows_pb, (int64_t(48) << 20) / (wave * std::max<int64_t>(row_bytes, 1)));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(rows_item / rows_pb, 4096 / rows_pb));
 }
 
 // Resolved tile of one SpMM argument record (as the launcher would pick it).
@@ -160,7 +172,7 @@ static void add_spmm(Batch* B, std::vector<BLaunch>& plan, const std::vector<Spm
       ga.push_back(a);
       const int S = (a.C / L.cpt) * L.kl;
       const int rows_pb = kBlock / S;
-      const int m = slots_per_item(a.rows, rows_pb, L.dot, (int64_t)a.C * (xt == VEC_F64 ? 8 : 4));
+      const int m = slots_per_item(a.rows, rows_pb, (int64_t)a.C * (xt == VEC_F64 ? 8 : 4));
       const int64_t slots = ((int64_t)a.rows + rows_pb - 1) / rows_pb;
       int32_t slot = 0;
       for (int64_t s0 = 0; s0 < slots; s0 += m, ++slot) {
@@ -173,10 +185,7 @@ static void add_spmm(Batch* B, std::vector<BLaunch>& plan, const std::vector<Spm
       }
       BDot bd;
       if (L.dot) {
-        bd.partials = a.dot.sc.partials;
-        bd.ticket = a.dot.sc.ticket;
-        bd.nslots = slot;
-        if ((int64_t)slot * a.C > a.dot.sc.partial_cap) fail(AMGSYM_ERR_STATE, "batched dot exceeds partial capacity");
+        bd = alloc_bdot(B, slot, a.C);
         smem_d = std::max(smem_d, sizeof(double) * (size_t)dot_smem_doubles(S, rows_pb, a.C));
       }
       dots.push_back(bd);
@@ -211,7 +220,7 @@ static void add_vec(Batch* B, std::vector<BLaunch>& plan, int op, VecType vt, co
     const UpdArgs& a = args[i];
     const int tpr = a.C / cpt;
     const int rows_pb = kBlock / tpr;
-    const int m = slots_per_item(a.rows, rows_pb, true, 0);
+    const int m = slots_per_item(a.rows, rows_pb, (int64_t)a.C * (vt == VEC_F64 ? 8 : 4));
     const int64_t slots = ((int64_t)a.rows + rows_pb - 1) / rows_pb;
     int32_t slot = 0;
     for (int64_t s0 = 0; s0 < slots; s0 += m, ++slot) {
@@ -224,9 +233,7 @@ static void add_vec(Batch* B, std::vector<BLaunch>& plan, int op, VecType vt, co
     }
     BDot bd;
     if (op == BOP_UPDATE1) {
-      bd.partials = a.dot.sc.partials;
-      bd.ticket = a.dot.sc.ticket;
-      bd.nslots = slot;
+      bd = alloc_bdot(B, slot, a.C);
       smem_d = std::max(smem_d, sizeof(double) * (size_t)dot_smem_doubles(tpr, rows_pb, a.C));
     }
     dots.push_back(bd);

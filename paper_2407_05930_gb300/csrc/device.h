@@ -185,10 +185,14 @@ struct BItem {
   int32_t slot;
 };
 
-// Where the dot partials of one problem's items go.
+// Where the dot partials of one problem's items go.  Two-level reduction:
+// items write partials[slot]; the last item of each chunk of 32 slots sums
+// them into chunk_partials[chunk]; the last chunk sums those and finalises.
 struct BDot {
-  double* partials = nullptr;
-  unsigned* ticket = nullptr;
+  double* partials = nullptr;        // [nslots][C]
+  double* chunk_partials = nullptr;  // [ceil(nslots / 32)][C]
+  unsigned* chunk_tickets = nullptr; // [ceil(nslots / 32)], zero between launches
+  unsigned* ticket = nullptr;        // zero between launches
   int32_t nslots = 0;
 };
 

@@ -174,4 +174,81 @@ __device__ __forceinline__ void block_dot(const DotArgs& d, double (&part)[CPT],
   __syncthreads();  // the block may go on to reuse the shared scratch
 }
 
+// Two-level variant for the batched kernels (see BDot): any number of items
+// per problem, each reduction stage reading at most 32 lines per column.
+template <int CPT>
+__device__ __forceinline__ void block_dot2(const DotArgs& d, double (&part)[CPT], int c0, bool has_cols, int rloc,
+                                           int rows_pb, int S, int C, double* sm, int slot, const BDot& bd) {
+  const bool pow2 = (S & (S - 1)) == 0 && S <= 32;
+  int lines;
+  if (pow2) {
+    for (int off = S; off < 32; off <<= 1) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) part[q] += __shfl_xor_sync(0xffffffffu, part[q], off);
+    }
+    lines = kBlock / 32;
+    const int lane = threadIdx.x & 31;
+    if (has_cols && lane < S) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) sm[(threadIdx.x >> 5) * C + c0 + q] = part[q];
+    }
+  } else {
+    lines = rows_pb;
+    if (has_cols) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) sm[rloc * C + c0 + q] = part[q];
+    }
+  }
+  __syncthreads();
+  const int slices = blockDim.x / C;
+  double* red = sm + lines * C;  // [slices][C]
+  // sum `count` lines of `src` (stride C) into red, then red over slices -> out
+  auto reduce_lines = [&](const double* src, int count, bool global_src, double* out) {
+    if ((int)threadIdx.x < slices * C) {
+      const int c = threadIdx.x % C, sl = threadIdx.x / C;
+      double t0 = 0.0, t1 = 0.0;
+      int r = sl;
+      for (; r + slices < count; r += 2 * slices) {
+        t0 += global_src ? __ldcg(src + (int64_t)r * C + c) : src[r * C + c];
+        t1 += global_src ? __ldcg(src + (int64_t)(r + slices) * C + c) : src[(r + slices) * C + c];
+      }
+      if (r < count) t0 += global_src ? __ldcg(src + (int64_t)r * C + c) : src[r * C + c];
+      red[sl * C + c] = t0 + t1;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+      double t = 0.0;
+      for (int sl = 0; sl < slices; ++sl) t += red[sl * C + c];
+      out[c] = t;
+    }
+  };
+  reduce_lines(sm, lines, false, bd.partials + (int64_t)slot * C);
+  __threadfence();
+  __syncthreads();
+  __shared__ unsigned last_chunk, last_all;
+  const int chunk = slot >> 5;
+  const int nch = (bd.nslots + 31) >> 5;
+  const int in_chunk = min(32, bd.nslots - chunk * 32);
+  if (threadIdx.x == 0) last_chunk = (atomicAdd(bd.chunk_tickets + chunk, 1u) == (unsigned)in_chunk - 1u) ? 1u : 0u;
+  __syncthreads();
+  if (!last_chunk) return;
+  __threadfence();
+  reduce_lines(bd.partials + (int64_t)chunk * 32 * C, in_chunk, true, bd.chunk_partials + (int64_t)chunk * C);
+  if (threadIdx.x == 0) bd.chunk_tickets[chunk] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last_all = (atomicAdd(bd.ticket, 1u) == (unsigned)nch - 1u) ? 1u : 0u;
+  __syncthreads();
+  if (!last_all) return;
+  __threadfence();
+  double* colsum = sm;  // [C] (the line area is free now)
+  reduce_lines(bd.chunk_partials, nch, true, colsum);
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) dot_finalize_column(d, c, colsum[c]);
+  __syncthreads();
+  dot_finalize_rhs(d, colsum);
+  if (threadIdx.x == 0) *bd.ticket = 0u;
+  __syncthreads();
+}
+
 }  // namespace amgsym

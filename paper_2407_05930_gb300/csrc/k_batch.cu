@@ -41,8 +41,7 @@ __global__ void __launch_bounds__(kBlock, 4)
 #pragma unroll
       for (int q = 0; q < CPT; ++q) part[q] = (t.slot_ok && t.e == 0) ? (double)dpart[q] : 0.0;
       const BDot bd = dots[bi.arg];
-      block_dot<CPT>(a.dot, part, t.c0, t.slot_ok && t.e == 0, t.g, t.rows_pb, t.S, a.C, sm, bi.slot, bd.nslots,
-                     bd.partials, bd.ticket);
+      block_dot2<CPT>(a.dot, part, t.c0, t.slot_ok && t.e == 0, t.g, t.rows_pb, t.S, a.C, sm, bi.slot, bd);
     }
   }
 }
@@ -191,8 +190,7 @@ __global__ void __launch_bounds__(kBlock) vec_batch_kernel(const UpdArgs* __rest
 #pragma unroll
       for (int k = 0; k < CPT; ++k) pd[k] = has_cols ? (double)part[k] : 0.0;
       const BDot bd = dots[bi.arg];
-      block_dot<CPT>(a.dot, pd, c0, has_cols, rloc, rows_pb, TPR, C, sm, bi.slot, bd.nslots, bd.partials,
-                     bd.ticket);
+      block_dot2<CPT>(a.dot, pd, c0, has_cols, rloc, rows_pb, TPR, C, sm, bi.slot, bd);
     }
   }
 }
