@@ -83,7 +83,8 @@ typedef struct {
   int32_t max_levels;       /* hierarchy depth limit, 25 */
   int32_t coarse_max;       /* dense direct solve at or below this size, 256 */
   int32_t fsai_max_lower;   /* FSAI pattern: strongest lower entries per row,
-                               diagonal included, default 8 */
+                               diagonal included, default 4 (the full lower
+                               pattern of a 7-point stencil) */
   double omega_scale;       /* smoother damping omega = omega_scale / lambda_max(G A G^T), 1.2 */
   int32_t nu;               /* V(nu, nu) cycle, default 1 */
   int32_t precisions;       /* bit mask of device copies to build:
@@ -103,7 +104,7 @@ typedef struct {
   int32_t use_x0;      /* 1: x_dev holds the initial guess; 0: start from zero */
   double inner_tol;    /* mixed: floor of the inner PCG relative reduction per
                           refinement step; the target of step k is
-                          clamp(tol / (4 relres_k), inner_tol, 0.5), 1e-5 */
+                          clamp(tol / (4 relres_k), inner_tol, 0.5), 1e-6 */
   int32_t max_outer;   /* mixed: refinement steps, 20 */
   int32_t finest_hat;  /* 1: V-cycle finest-level residuals use A^_i instead of A_inn */
   int32_t use_graph;   /* 1: capture one PCG iteration in a CUDA graph and replay it */

@@ -52,7 +52,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->interp_max_elems = 4;
   o->max_levels = 25;
   o->coarse_max = 256;
-  o->fsai_max_lower = 8;
+  o->fsai_max_lower = 4;
   o->omega_scale = 1.2;
   o->nu = 1;
   o->precisions = 3;
@@ -67,7 +67,7 @@ extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {
   o->maxit = 500;
   o->precision = AMGSYM_PREC_FP64;
   o->use_x0 = 0;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 1e-6;
   o->max_outer = 20;
   o->finest_hat = 0;
   o->use_graph = 1;
