@@ -35,6 +35,24 @@ if ROOT not in sys.path:
 from synth import CONFIGS, batched_problem_specs, gaussian_logk, rhs_uniform  # noqa: E402
 
 METRIC = "AMG-PCG solves/s + SpMM HBM GB/s, 256^3 s=3, mixed vs FP64 at rel-res 1e-8"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the reduced SpMM on this workload, from an ncu capture of the kernel sources
+# with this SHA-256 (profiles/spmm_reduced_fp32_256cube_s3.md).  Reported as
+# roofline.traffic only while the sources are unchanged.
+SPMM_TRAFFIC_BYTES = 239.8e6
+SPMM_SOURCES = ("paper_2407_05930_gb300/csrc/k_spmm.cu", "paper_2407_05930_gb300/csrc/spmm_common.cuh")
+SPMM_SOURCES_SHA256 = "bfe9f6a21cdc09f61e84bd2b8c5039f17e52c31c59ac5d7c440ed0925dfc436d"
+
+
+def _spmm_sources_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in SPMM_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 CFG = CONFIGS[3]
 FIELD_SEED = 3000
 
@@ -362,7 +380,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": "spmm_kernel<float,float,float> (reduced SpMM, interface fused)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "algo_bytes_per_launch": algo, "launch_us": t_k * 1e6,
-                     "traffic": None},
+                     "traffic": SPMM_TRAFFIC_BYTES if _spmm_sources_sha() == SPMM_SOURCES_SHA256 else None},
         "gpu_launches": int(launches_m),
         "clocks": clocks,
         "setup_s": t_setup,
