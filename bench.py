@@ -66,6 +66,23 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(sec: float, device=None) -> float:
+    """The slowest rank's time (replicas: the job finishes with the last one)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return sec
+    t = torch.tensor([sec], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: float, sec_max: float, world: int) -> float:
+    """Whole-job rate of `world` independent replicas: all units over the max time."""
+    return world * units_per_rank / sec_max
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -291,11 +308,7 @@ def run_gpu(args):
         e1.record(st)
         torch.cuda.synchronize()
         barrier()
-        sec = e0.elapsed_time(e1) * 1e-3
-        if ws > 1:
-            t = torch.tensor([sec], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            sec = float(t.item())
+        sec = max_over_ranks(e0.elapsed_time(e1) * 1e-3, dev)
         return sec, amg.kernel_launches() - l0
 
     nvtx = torch.cuda.nvtx
@@ -324,11 +337,7 @@ def run_gpu(args):
         x_pin.copy_(x, non_blocking=True)
     e1.record(st)
     torch.cuda.synchronize()
-    sec_e = e0.elapsed_time(e1) * 1e-3
-    if ws > 1:
-        t = torch.tensor([sec_e], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        sec_e = float(t.item())
+    sec_e = max_over_ranks(e0.elapsed_time(e1) * 1e-3, dev)
 
     # variant: finest-level V-cycle residuals with the interface-corrected
     # blocks A^_i instead of A_inn (same hierarchy)
@@ -348,7 +357,7 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     achieved = algo / t_k / 1e9
 
-    value = ws * nrhs * args.steps / sec_m
+    value = replica_rate(nrhs * args.steps, sec_m, ws)
     line = {
         "metric": METRIC,
         "value": value,
