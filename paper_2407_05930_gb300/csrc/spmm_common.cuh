@@ -119,32 +119,34 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
     if (live) {
       const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
       int k = kb + e;
-      // U entries per step: all index/value loads first, then all gathers,
-      // so U gathers of this lane are in flight at once
+      // U entries per step, predicated: all index/value loads first, then all
+      // gathers, so a row of up to U * KL entries costs one round trip and a
+      // 7-point row (U = 4) two, with every gather of a step in flight at once
       constexpr int U = CPT >= 8 ? 2 : 4;
-      for (; k + (U - 1) * KL < ke; k += U * KL) {
+      for (; k < ke; k += U * KL) {
         int j[U];
         CT m[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          j[u] = __ldg(idx + k + u * KL);
-          m[u] = cvt<CT>(val[k + u * KL]);
+          const bool ok = k + u * KL < ke;
+          j[u] = ok ? __ldg(idx + k + u * KL) : 0;
+          m[u] = ok ? cvt<CT>(val[k + u * KL]) : (CT)0;
         }
         Vec<XT, CPT> x[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) x[u] = ldv<XT, CPT>(X + (int64_t)j[u] * C + c0);
+        for (int u = 0; u < U; ++u) {
+          if (k + u * KL < ke) {
+            x[u] = ldv<XT, CPT>(X + (int64_t)j[u] * C + c0);
+          } else {
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) x[u].v[q] = (XT)0;
+          }
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
 #pragma unroll
           for (int q = 0; q < CPT; ++q) acc[q] = fma(m[u], (CT)x[u].v[q], acc[q]);
         }
-      }
-      for (; k < ke; k += KL) {
-        const int j0 = __ldg(idx + k);
-        const CT m0 = cvt<CT>(val[k]);
-        const Vec<XT, CPT> x0 = ldv<XT, CPT>(X + (int64_t)j0 * C + c0);
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) acc[q] = fma(m0, (CT)x0.v[q], acc[q]);
       }
       if (HAS_IFACE && e == 0) {
         const uint32_t wd = __ldg(a.imask + (row >> 5));
