@@ -26,7 +26,7 @@
 namespace amgsym {
 
 template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE>
-__global__ void __launch_bounds__(kBlock, (CPT >= 8 ? 4 : HAS_DOT ? 6 : 8)) spmm_kernel(SpmmArgs a) {
+__global__ void __launch_bounds__(kBlock, (CPT >= 8 ? 4 : (HAS_DOT || HAS_IFACE) ? 6 : 8)) spmm_kernel(SpmmArgs a) {
   using DT = typename AccOf<XT>::type;
   if (a.skip && *a.skip == 0) return;  // uniform over the grid
   DT dpart[CPT];

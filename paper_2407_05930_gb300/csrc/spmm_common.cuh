@@ -91,6 +91,9 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
                                           typename AccOf<XT>::type (&dpart)[CPT]) {
   using CT = typename ComputeOf<MT, XT>::type;
   using DT = typename AccOf<XT>::type;  // per-thread dot partial type
+  // Early epilogue-operand load only where the register budget allows it
+  // without spills (the variants launched at 6 blocks per SM).
+  constexpr bool ZPF = HAS_DOT || HAS_IFACE;
   const int C = a.C;
   const int TPC = C / CPT;
   const int S = TPC * KL;
@@ -116,8 +119,13 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
     CT acc[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
+    Vec<XT, CPT> zpre;
     if (live) {
       const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
+      // interface flag word and epilogue operand loaded with the row pointers,
+      // off the critical path of the gathers
+      const uint32_t iface_word = (HAS_IFACE && e == 0) ? __ldg(a.imask + (row >> 5)) : 0u;
+      if (ZPF && e == 0 && a.beta != 0.0) zpre = ldv<XT, CPT>(Z + (int64_t)row * C + c0);
       int k = kb + e;
       // U entries per step, predicated: all index/value loads first, then all
       // gathers, so a row of up to U * KL entries costs one round trip and a
@@ -149,7 +157,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
         }
       }
       if (HAS_IFACE && e == 0) {
-        const uint32_t wd = __ldg(a.imask + (row >> 5));
+        const uint32_t wd = iface_word;
         const uint32_t bit = 1u << (row & 31);
         if (wd & bit) {
           const int f = __ldg(a.iprefix + (row >> 5)) + __popc(wd & (bit - 1u));
@@ -176,7 +184,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
     if (live && e == 0) {
       Vec<OT, CPT> out;
       if (a.beta != 0.0) {
-        const Vec<XT, CPT> zv = ldv<XT, CPT>(Z + (int64_t)row * C + c0);
+        const Vec<XT, CPT> zv = ZPF ? zpre : ldv<XT, CPT>(Z + (int64_t)row * C + c0);
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
           const CT y = alpha * acc[q] + beta * (CT)zv.v[q];
