@@ -42,7 +42,7 @@ METRIC = "AMG-PCG solves/s + SpMM HBM GB/s, 256^3 s=3, mixed vs FP64 at rel-res 
 # roofline.traffic only while the sources are unchanged.
 SPMM_TRAFFIC_BYTES = 239.8e6
 SPMM_SOURCES = ("paper_2407_05930_gb300/csrc/k_spmm.cu", "paper_2407_05930_gb300/csrc/spmm_common.cuh")
-SPMM_SOURCES_SHA256 = "bfe9f6a21cdc09f61e84bd2b8c5039f17e52c31c59ac5d7c440ed0925dfc436d"
+SPMM_SOURCES_SHA256 = "f6103caa9afa6791f4aed0bf2fe9db0ee227a63e1bac110f191530824f032088"
 
 
 def _spmm_sources_sha():

@@ -113,15 +113,36 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
   const CT alpha = (CT)a.alpha, beta = (CT)a.beta;
 
   // The trip count is block-uniform (the shuffles need every lane of the warp).
-  for (int base = first_slot * rows_pb; base < row_end; base += slot_step * rows_pb) {
+  // In the variants with registers to spare (ZPF), the row pointers of a
+  // thread's next row are loaded one iteration ahead, which takes one
+  // dependent load off each row's chain.
+  const int step_rows = slot_step * rows_pb;
+  int kb_next = 0, ke_next = 0;
+  if (ZPF) {
+    const int row0 = first_slot * rows_pb + g;
+    if (slot_ok && row0 < row_end) {
+      kb_next = __ldg(ptr + row0);
+      ke_next = __ldg(ptr + row0 + 1);
+    }
+  }
+  for (int base = first_slot * rows_pb; base < row_end; base += step_rows) {
     const int row = base + g;
     const bool live = slot_ok && row < row_end;
     CT acc[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
     Vec<XT, CPT> zpre;
+    int kb = kb_next, ke = ke_next;
+    if (ZPF) {
+      if (slot_ok && row + step_rows < row_end) {
+        kb_next = __ldg(ptr + row + step_rows);
+        ke_next = __ldg(ptr + row + step_rows + 1);
+      }
+    } else if (live) {
+      kb = __ldg(ptr + row);
+      ke = __ldg(ptr + row + 1);
+    }
     if (live) {
-      const int kb = __ldg(ptr + row), ke = __ldg(ptr + row + 1);
       // interface flag word and epilogue operand loaded with the row pointers,
       // off the critical path of the gathers
       const uint32_t iface_word = (HAS_IFACE && e == 0) ? __ldg(a.imask + (row >> 5)) : 0u;
