@@ -428,7 +428,7 @@ def run_batched(args):
         bs.append(torch.from_numpy(rhs_uniform(P.n, 16, config=4000 + k)).to(dev))
     t_setup = time.time() - t0
     B = amg.Batch(probs, [16] * len(probs))
-    kw = dict(tol=1e-8, precision=amg.PREC_MIXED_FP32)
+    kw = dict(tol=1e-8, precision=amg.PREC_MIXED_FP32, tune=0 if args.no_tune else 1)
     xs = [torch.empty_like(b) for b in bs]
     for _ in range(args.warmup):
         _, res = B.solve(bs, xs, **kw)
@@ -469,6 +469,7 @@ def run_batched(args):
         "config": {"workload": CONFIGS[4]["name"], "problems": len(probs),
                    "cells": int(sum(p.n for p in probs)), "rhs_per_problem": 16,
                    "sizes": [sp["N"][0] for sp in specs], "s": [sp["s"] for sp in specs]},
+        "tiles": "fixed from row lengths" if args.no_tune else "autotuned per problem and matrix",
         "inner_iters": res[0].iters, "outer_iters": res[0].outer_iters,
         "max_relres": float(max(np.max(r.relres) for r in res)), "all_converged": all(r.converged for r in res),
         "fp64_sequential": {"value": nsolves / sec64, "unit": "solves/s",
@@ -489,6 +490,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["256cube", "batched"], default="256cube")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--no-tune", action="store_true", help="batched: fixed tiles instead of the autotuner")
     ap.add_argument("--fp64-sample", type=int, default=8)
     ap.add_argument("--profile-only", choices=["mixed", "fp64"], default=None,
                     help="run one marked solve and the roofline SpMM only (for ncu)")

@@ -109,8 +109,10 @@ typedef struct {
   int32_t finest_hat;  /* 1: V-cycle finest-level residuals use A^_i instead of A_inn */
   int32_t use_graph;   /* 1: capture one PCG iteration in a CUDA graph and replay it */
   int32_t tune;        /* 1: time the SpMM tile candidates of every matrix once per
-                          column count and precision before the first PCG loop
-                          (default); 0: fixed tiles from the row lengths */
+                          column count and precision before the first PCG loop and
+                          keep the fastest (results are then reproducible only for
+                          the same tile choice); 0 (default): fixed tiles from the
+                          row lengths, bit-reproducible from run to run */
 } amgsym_solve_opts;
 
 typedef struct {
@@ -317,6 +319,13 @@ amgsym_status amgsym_batch_create(const amgsym_t* problems, int32_t count, const
 amgsym_status amgsym_batch_solve(amgsym_batch_t b, const double* const* b_dev, double* const* x_dev,
                                  const amgsym_solve_opts* sopts, void* stream, amgsym_solve_info* infos);
 void amgsym_batch_destroy(amgsym_batch_t b);
+
+/* SpMM tiles in use for nrhs right-hand sides and precision prec (after a
+ * solve with sopts->tune = 1 these are the tuner's choices, else the fixed
+ * ones): out[0..1] = (columns per thread, entry lanes) of the reduced
+ * operator, then for each level l < max_levels five pairs for A_l, G_l, G_l^T,
+ * R_l, P_l (0, 0 where absent).  out holds 2 + 10 * max_levels int32. */
+amgsym_status amgsym_get_tiles(amgsym_t h, int32_t nrhs, int32_t prec, int32_t* out, int32_t max_levels);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (a replayed CUDA graph counts its kernels).  Host-side counter. */

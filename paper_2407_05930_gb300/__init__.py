@@ -124,6 +124,7 @@ def _load():
         "amgsym_mirror_perm": (i32, [i32, pi64, i32, pi32]),
         "amgsym_fv_grad_logk": (i32, [i32, pi64, P, P, P, P, i32, i64, P, i32, P]),
         "amgsym_kernel_launches": (i64, []),
+        "amgsym_get_tiles": (i32, [P, i32, i32, pi32, i32]),
         "amgsym_batch_create": (i32, [ctypes.POINTER(P), i32, pi32, ctypes.POINTER(P)]),
         "amgsym_batch_solve": (i32, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(SolveOpts), P,
                                      ctypes.POINTER(SolveInfo)]),
@@ -149,7 +150,7 @@ EXPORTED = [
         "amgsym_solve_adjoint amgsym_transform_forward amgsym_transform_backward "
         "amgsym_apply_reduced amgsym_vcycle amgsym_vcycle_noalloc amgsym_grid_widths amgsym_fv_nnz "
         "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy "
-        "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy"
+        "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles"
     ).split()
 ]
 
@@ -387,6 +388,18 @@ class Problem:
         _check(lib.amgsym_apply_reduced(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
                                         nrhs, prec, self._stream()))
         return Y
+
+    def tiles(self, nrhs: int = 1, prec: int = PREC_MIXED_FP32, max_levels: int = 16):
+        """SpMM tiles (columns per thread, entry lanes) in use: {'K3': (..), 'levels': [{A,G,Gt,R,P}]}."""
+        out = np.zeros(2 + 10 * max_levels, dtype=np.int32)
+        _check(lib.amgsym_get_tiles(self._h, nrhs, prec, _ptr(out, ctypes.c_int32), max_levels))
+        levels = []
+        for l in range(max_levels):
+            v = out[2 + 10 * l: 12 + 10 * l].reshape(5, 2)
+            if not v.any():
+                break
+            levels.append({k: tuple(int(t) for t in v[i]) for i, k in enumerate(["A", "G", "Gt", "R", "P"])})
+        return {"K3": (int(out[0]), int(out[1])), "levels": levels}
 
     def vcycle_noalloc(self, R, Z, nrhs: int, prec: int = PREC_FP64, finest_hat: bool = False):
         """The V-cycle with its work vectors in the library's fixed device

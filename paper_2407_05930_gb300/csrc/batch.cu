@@ -61,6 +61,10 @@ struct Batch {
   int64_t graph_kernels = 0;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  // batched autotuner: on while plans are built with sopts->tune = 1
+  bool tune = false;
+  cudaStream_t tune_stream = nullptr;
+  std::map<std::vector<const void*>, std::pair<int, int>> tuned;  // matrices of a step -> (cpt, kl)
 };
 
 #define BCK(call)                                                                          \
@@ -146,9 +150,12 @@ static void resolve_tile(const SpmmArgs& a, VecType xt, VecType ot, int* cpt, in
   *kl = k;
 }
 
+static void run_plan(const std::vector<BLaunch>& plan, cudaStream_t st);
+
 // One batched SpMM step: args[p] for each taking part problem (DotArgs inside).
-static void add_spmm(Batch* B, std::vector<BLaunch>& plan, const std::vector<SpmmArgs>& args, ValType mt, VecType xt,
-                     VecType ot) {
+// Device arrays of the launches go to `owner`.
+static void add_spmm_core(Batch* B, std::vector<BLaunch>& plan, const std::vector<SpmmArgs>& args, ValType mt,
+                          VecType xt, VecType ot, std::vector<void*>& owner) {
   std::map<std::tuple<int, int, bool, bool>, std::vector<int>> groups;
   std::vector<int> cpts(args.size()), kls(args.size());
   for (size_t i = 0; i < args.size(); ++i) {
@@ -193,13 +200,69 @@ static void add_spmm(Batch* B, std::vector<BLaunch>& plan, const std::vector<Spm
     // items stay in row order problem by problem: a wave of blocks then
     // sweeps contiguous row windows, so far-neighbour gathers hit L2
     std::vector<BItem> mixed = items;
-    L.args = bupload(B->plan_owned, ga);
-    L.items = bupload(B->plan_owned, mixed);
-    L.dots = bupload(B->plan_owned, dots);
+    L.args = bupload(owner, ga);
+    L.items = bupload(owner, mixed);
+    L.dots = bupload(owner, dots);
     L.n_items = (int32_t)mixed.size();
     L.smem = smem_d;
     plan.push_back(L);
   }
+}
+
+// The batched autotuner: for a step without fused dots, time the whole
+// batched step (every problem taking part) under each candidate tile --
+// columns per thread (one or two 16-byte vectors) x entry lanes (1..16),
+// clamped per problem to what its column count allows -- and keep the
+// fastest.  Steps over the same matrices (pre- and post-smoothing) share the
+// choice.  Timing runs the real work arrays (their contents do not matter).
+static void add_spmm(Batch* B, std::vector<BLaunch>& plan, std::vector<SpmmArgs> args, ValType mt, VecType xt,
+                     VecType ot) {
+  bool dot = false;
+  for (const SpmmArgs& a : args) dot = dot || a.dot.mode != DOT_NONE;
+  if (B->tune && !dot && !args.empty()) {
+    std::vector<const void*> key;
+    for (const SpmmArgs& a : args) key.push_back(a.idx);
+    auto it = B->tuned.find(key);
+    if (it == B->tuned.end()) {
+      const int V = (xt == VEC_F64 || ot == VEC_F64) ? 2 : 4;
+      cudaEvent_t e0, e1;
+      BCK(cudaEventCreate(&e0));
+      BCK(cudaEventCreate(&e1));
+      float best_ms = 1e30f;
+      std::pair<int, int> best(0, 0);
+      for (int cm = 1; cm <= 2; ++cm)
+        for (int kl = 1; kl <= 16; kl *= 2) {
+          std::vector<SpmmArgs> cand = args;
+          for (SpmmArgs& a : cand) {
+            a.cpt = V * cm;
+            a.kl = kl;
+          }
+          std::vector<BLaunch> tmp;
+          std::vector<void*> tmp_owned;
+          add_spmm_core(B, tmp, cand, mt, xt, ot, tmp_owned);
+          run_plan(tmp, B->tune_stream);  // warm-up
+          BCK(cudaEventRecord(e0, B->tune_stream));
+          for (int r = 0; r < 3; ++r) run_plan(tmp, B->tune_stream);
+          BCK(cudaEventRecord(e1, B->tune_stream));
+          BCK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          BCK(cudaEventElapsedTime(&ms, e0, e1));
+          for (void* q : tmp_owned) cudaFree(q);
+          if (ms < best_ms * 0.97f) {
+            best_ms = ms;
+            best = {V * cm, kl};
+          }
+        }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      it = B->tuned.emplace(key, best).first;
+    }
+    for (SpmmArgs& a : args) {
+      a.cpt = it->second.first;
+      a.kl = it->second.second;
+    }
+  }
+  add_spmm_core(B, plan, args, mt, xt, ot, B->plan_owned);
 }
 
 static void add_vec(Batch* B, std::vector<BLaunch>& plan, int op, VecType vt, const std::vector<UpdArgs>& args) {
@@ -463,6 +526,7 @@ static void batch_free(Batch* B) {
   if (B->h_tol2) cudaFreeHost(B->h_tol2);
   if (B->h_relres) cudaFreeHost(B->h_relres);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+  if (B->tune_stream) cudaStreamDestroy(B->tune_stream);
   for (auto& e : B->ev)
     if (e) cudaEventDestroy(e);
   delete B;
@@ -509,13 +573,21 @@ static amgsym_status batch_solve_impl(Batch* B, const double* const* b_dev, doub
   std::vector<uint64_t> gens(n);
   for (int p = 0; p < n; ++p) gens[p] = ctx[p].D->work_gen;
   if (B->planned_key != key || B->planned_gen != gens) {
-    if (o.tune)
-      for (int p = 0; p < n; ++p) {
-        Ctx c = ctx[p];
-        c.skip = nullptr;
-        tune_tiles(c);
-      }
+    B->tune = o.tune != 0;
+    B->tuned.clear();
+    BCK(cudaStreamSynchronize(st));  // no earlier work of this batch in flight
+    if (B->tune) {
+      // the timed steps must not skip: mark every problem active meanwhile
+      std::vector<int32_t> act(4 * n, 0);
+      for (int p = 0; p < n; ++p) act[4 * p] = 1;
+      BCK(cudaMemcpy(B->status_in, act.data(), sizeof(int32_t) * 4 * n, cudaMemcpyHostToDevice));
+    }
     build_plans(B, ctx, key);
+    if (B->tune) {
+      BCK(cudaStreamSynchronize(B->tune_stream));
+      BCK(cudaMemset(B->status_in, 0, sizeof(int32_t) * 4 * n));
+      B->tune = false;
+    }
     for (int p = 0; p < n; ++p) gens[p] = ctx[p].D->work_gen;  // tuning allocates nothing, but be exact
     B->planned_gen = gens;
   }
@@ -703,6 +775,7 @@ extern "C" amgsym_status amgsym_batch_create(const amgsym_t* problems, int32_t c
     for (int p = 0; p < count; ++p) nr += nrhs[p];
     BCK(cudaMallocHost(&B->h_relres, sizeof(double) * nr));
     BCK(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+    BCK(cudaStreamCreateWithFlags(&B->tune_stream, cudaStreamNonBlocking));
     BCK(cudaEventCreateWithFlags(&B->ev[0], cudaEventDisableTiming));
     BCK(cudaEventCreateWithFlags(&B->ev[1], cudaEventDisableTiming));
     auto* h = new amgsym_batch();

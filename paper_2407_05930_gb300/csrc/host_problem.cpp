@@ -71,7 +71,7 @@ extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {
   o->max_outer = 20;
   o->finest_hat = 0;
   o->use_graph = 1;
-  o->tune = 1;
+  o->tune = 0;
 }
 
 // Sign of entry (i, j) of the Sylvester-Hadamard matrix 2^{s/2} P_s (eq. "P_s").

@@ -226,17 +226,37 @@ void ensure_work(Device* D, int32_t nrhs, VecType vt) {
 // ---------------------------------------------------------------------------
 // Kernel sequencing.
 
-// Entry lanes per row: one lane for short rows (fine-level stencils, where
-// the L1-resident neighbours keep the gathers cheap), then about 5 entries per
-// lane for the longer rows of the coarse Galerkin operators, at most 32
-// threads per row.
-int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt) {
-  const int cpt = xt == VEC_F64 ? 2 : 4;
-  const int tpc = (C % cpt == 0) ? C / cpt : C;
-  int kl = 1;
-  while (kl < 16 && M.avg_row >= 10.0 * kl && tpc * kl * 2 <= 32) kl *= 2;
-  return kl;
+// Fixed tile from the row length (what the autotuner picks on the 256^3
+// workload, measured on GB300): short rows take one thread per row holding
+// two 16-byte vectors of columns (coalesced index/value loads for a warp of
+// consecutive rows); medium rows split their entries over 4 lanes; the long
+// rows of the coarse Galerkin operators over 4-16 lanes with one vector each.
+Tile fixed_tile(const DevCsr& M, int32_t C, VecType xt) {
+  const int V = xt == VEC_F64 ? 2 : 4;
+  const bool two = C % (2 * V) == 0 && C / (2 * V) >= 1;
+  Tile t;
+  const double r = M.avg_row;
+  if (r < 10.0) {
+    t.cpt = two ? 2 * V : V;
+    t.kl = 1;
+  } else if (r < 32.0) {
+    t.cpt = two ? 2 * V : V;
+    t.kl = 4;
+  } else if (r < 60.0) {
+    t.cpt = V;
+    t.kl = 4;
+  } else {
+    t.cpt = V;
+    t.kl = 16;
+  }
+  if (C % t.cpt) t.cpt = (C % V == 0) ? V : 1;
+  const int tpc = C / t.cpt;
+  if (tpc & (tpc - 1)) t.kl = 1;
+  while (t.kl > 1 && tpc * t.kl > 32) t.kl >>= 1;
+  return t;
 }
+
+int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt) { return fixed_tile(M, C, xt).kl; }
 
 SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X,
                         void* Y, double alpha, double beta, const void* Z, bool iface, const DotArgs* dot) {
@@ -268,7 +288,9 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
     a.kl = it->second.kl;
     a.cpt = it->second.cpt;
   } else {
-    a.kl = entry_lanes(M, c.C, xt);
+    const Tile t = fixed_tile(M, c.C, xt);
+    a.kl = t.kl;
+    a.cpt = t.cpt;
   }
   return a;
 }
@@ -883,5 +905,37 @@ extern "C" amgsym_status amgsym_vcycle_noalloc(amgsym_t h, const void* R_dev, vo
   }
   Ctx c{D, C, vt, mt, finest_hat != 0, (cudaStream_t)stream};
   vcycle_with(c, lws, 0, R_dev, Z_dev);
+  API_END
+}
+
+extern "C" amgsym_status amgsym_get_tiles(amgsym_t h, int32_t nrhs, int32_t prec, int32_t* out, int32_t max_levels) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (!out || max_levels < 1) fail(AMGSYM_ERR_ARG, "bad output buffer");
+  const int32_t C = nrhs * D->nb;
+  const bool f64 = prec == AMGSYM_PREC_FP64;
+  const VecType vt = f64 ? VEC_F64 : VEC_F32;
+  const ValType mt = f64 ? VAL_F64 : prec == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : VAL_F32;
+  Ctx c{D, C, vt, mt, false, nullptr};
+  auto put = [&](int slot, const DevCsr& M, ValType m) {
+    if (!M.idx) {
+      out[2 * slot] = out[2 * slot + 1] = 0;
+      return;
+    }
+    const SpmmArgs a = make_spmm_args(c, M, m, vt, vt, nullptr, nullptr, 1.0, 0.0, nullptr, false, nullptr);
+    out[2 * slot] = a.cpt;
+    out[2 * slot + 1] = a.kl;
+  };
+  put(0, D->Ainn, f64 ? VAL_F64 : VAL_F32);
+  for (int l = 0; l < max_levels; ++l) {
+    const bool have = l < (int)D->lv.size() && !D->lv[l].cinv;
+    const DevLevel empty;
+    const DevLevel& L = have ? D->lv[l] : empty;
+    put(1 + 5 * l + 0, L.A, mt);
+    put(1 + 5 * l + 1, L.G, mt);
+    put(1 + 5 * l + 2, L.Gt, mt);
+    put(1 + 5 * l + 3, L.R, mt);
+    put(1 + 5 * l + 4, L.P, mt);
+  }
   API_END
 }
