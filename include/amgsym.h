@@ -94,7 +94,7 @@ typedef struct {
   uint64_t seed;            /* PMIS random tie-breaking, default 12345 */
   double coarse_drop;       /* sparsified Galerkin operators below the finest level:
                                drop a_ij with |a_ij| < coarse_drop sqrt(a_ii a_jj),
-                               adding it to a_ii (0 = exact Galerkin), default 0 */
+                               adding it to a_ii (0 = exact Galerkin), default 0.003 */
 } amgsym_opts;
 
 typedef struct {

@@ -58,7 +58,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->precisions = 3;
   o->host_only = 0;
   o->seed = 12345;
-  o->coarse_drop = 0.0;
+  o->coarse_drop = 0.003;
 }
 
 extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {
