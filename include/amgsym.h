@@ -95,7 +95,17 @@ typedef struct {
   double coarse_drop;       /* sparsified Galerkin operators below the finest level:
                                drop a_ij with |a_ij| < coarse_drop sqrt(a_ii a_jj),
                                adding it to a_ii (0 = exact Galerkin), default 0.003 */
+  int32_t dia_max_diag;     /* device storage of A_l, G_l, G_l^T: a matrix whose entries
+                               lie on at most this many diagonals (column offsets j - i),
+                               with at most 25 % padding, is also stored by diagonals and
+                               its products read no column indices (a structured-grid
+                               stencil: 7 diagonals in 3-D, 4 for its FSAI factor).  An
+                               exactly symmetric one stores its lower half only.  The sums
+                               run in the CSR order, so results are bit-identical to the
+                               CSR kernels.  0 = CSR only; default 8 = AMGSYM_MAX_DIAG */
 } amgsym_opts;
+
+#define AMGSYM_MAX_DIAG 8
 
 typedef struct {
   double tol;          /* stop when ||b - A x||_2 / ||b||_2 <= tol per RHS, 1e-8 */
@@ -181,6 +191,14 @@ amgsym_status amgsym_level_sizes(amgsym_t h, int32_t level, int64_t* rows, int64
                                  int64_t* nnz_P, int64_t* cols_P, int64_t* nnz_G, double* omega);
 amgsym_status amgsym_get_level_matrix(amgsym_t h, int32_t level, int32_t which,
                                       int64_t* rowptr, int32_t* colidx, double* vals);
+/* Diagonal-offset form of a level matrix (opts->dia_max_diag): which = 0 A_l,
+ * 2 G_l, 3 G_l^T.  *ndiag = number of diagonals (0: the matrix is CSR only),
+ * *nstored = value arrays stored (fewer than *ndiag when the matrix is exactly
+ * symmetric), offsets[AMGSYM_MAX_DIAG] = the column offsets ascending, zero
+ * padded.  Any output may be NULL.  Errors: AMGSYM_ERR_STATE without a
+ * hierarchy, AMGSYM_ERR_ARG for a bad level or which. */
+amgsym_status amgsym_level_dia(amgsym_t h, int32_t level, int32_t which, int32_t* ndiag,
+                               int32_t* nstored, int32_t* offsets);
 
 /* ------------------------------------------------------------------------
  * Solve (Alg. 1): x = A^{-1} b for nrhs right-hand sides.

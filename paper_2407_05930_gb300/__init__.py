@@ -61,6 +61,7 @@ class Opts(ctypes.Structure):
         ("host_only", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("coarse_drop", ctypes.c_double),
+        ("dia_max_diag", ctypes.c_int32),
     ]
 
 
@@ -111,6 +112,7 @@ def _load():
         "amgsym_num_levels": (i32, [P]),
         "amgsym_level_sizes": (i32, [P, i32, pi64, pi64, pi64, pi64, pi64, pdbl]),
         "amgsym_get_level_matrix": (i32, [P, i32, i32, pi64, pi32, pdbl]),
+        "amgsym_level_dia": (i32, [P, i32, i32, pi32, pi32, pi32]),
         "amgsym_solve": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
         "amgsym_solve_adjoint": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
         "amgsym_transform_forward": (i32, [P, P, i32, i64, P, P]),
@@ -150,7 +152,7 @@ EXPORTED = [
         "amgsym_solve_adjoint amgsym_transform_forward amgsym_transform_backward "
         "amgsym_apply_reduced amgsym_vcycle amgsym_vcycle_noalloc amgsym_grid_widths amgsym_fv_nnz "
         "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy "
-        "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles"
+        "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles amgsym_level_dia"
     ).split()
 ]
 
@@ -334,6 +336,15 @@ class Problem:
         _check(lib.amgsym_get_level_matrix(self._h, level, w, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32),
                                            _ptr(v, ctypes.c_double)))
         return rp, ci[:nnz], v[:nnz], (rows, cols)
+
+    def level_dia(self, level: int, which: str):
+        """Diagonal-offset form of A, G or Gt on a level: {'ndiag', 'nstored', 'offsets'}
+        (ndiag = 0: CSR only)."""
+        w = {"A": 0, "G": 2, "Gt": 3}[which]
+        nd, ns = ctypes.c_int32(), ctypes.c_int32()
+        off = np.zeros(8, dtype=np.int32)
+        _check(lib.amgsym_level_dia(self._h, level, w, ctypes.byref(nd), ctypes.byref(ns), _ptr(off, ctypes.c_int32)))
+        return dict(ndiag=nd.value, nstored=ns.value, offsets=[int(v) for v in off[: nd.value]])
 
     # ---------------------------------------------------------------- device
     @staticmethod

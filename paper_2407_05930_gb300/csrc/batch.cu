@@ -31,7 +31,7 @@ struct BLaunch {
   ValType mt = VAL_F32;
   VecType xt = VEC_F32, ot = VEC_F32;
   int cpt = 4, kl = 1, op = 0;
-  bool dot = false, ifc = false;
+  bool dot = false, ifc = false, dia = false;
   void* args = nullptr;
   BItem* items = nullptr;
   BDot* dots = nullptr;
@@ -144,7 +144,7 @@ static void resolve_tile(const SpmmArgs& a, VecType xt, VecType ot, int* cpt, in
   if (xt == VEC_F64 || ot == VEC_F64) c = std::min(c, xt == VEC_F64 && ot == VEC_F64 ? 4 : 2);
   const int tpc = a.C / c;
   int k = a.kl > 0 ? a.kl : 1;
-  if (tpc & (tpc - 1)) k = 1;
+  if ((tpc & (tpc - 1)) || a.ndiag > 0) k = 1;
   while (k > 1 && tpc * k > 32) k >>= 1;
   *cpt = c;
   *kl = k;
@@ -156,11 +156,13 @@ static void run_plan(const std::vector<BLaunch>& plan, cudaStream_t st);
 // Device arrays of the launches go to `owner`.
 static void add_spmm_core(Batch* B, std::vector<BLaunch>& plan, const std::vector<SpmmArgs>& args, ValType mt,
                           VecType xt, VecType ot, std::vector<void*>& owner) {
-  std::map<std::tuple<int, int, bool, bool>, std::vector<int>> groups;
+  std::map<std::tuple<int, int, bool, bool, bool>, std::vector<int>> groups;
   std::vector<int> cpts(args.size()), kls(args.size());
   for (size_t i = 0; i < args.size(); ++i) {
     resolve_tile(args[i], xt, ot, &cpts[i], &kls[i]);
-    groups[std::make_tuple(cpts[i], kls[i], args[i].dot.mode != DOT_NONE, args[i].imask != nullptr)].push_back((int)i);
+    groups[std::make_tuple(cpts[i], kls[i], args[i].dot.mode != DOT_NONE, args[i].imask != nullptr,
+                           args[i].ndiag > 0)]
+        .push_back((int)i);
   }
   for (auto& kv : groups) {
     BLaunch L;
@@ -168,7 +170,7 @@ static void add_spmm_core(Batch* B, std::vector<BLaunch>& plan, const std::vecto
     L.mt = mt;
     L.xt = xt;
     L.ot = ot;
-    std::tie(L.cpt, L.kl, L.dot, L.ifc) = kv.first;
+    std::tie(L.cpt, L.kl, L.dot, L.ifc, L.dia) = kv.first;
     std::vector<SpmmArgs> ga;
     std::vector<BItem> items;
     std::vector<BDot> dots;
@@ -230,8 +232,10 @@ static void add_spmm(Batch* B, std::vector<BLaunch>& plan, std::vector<SpmmArgs>
       BCK(cudaEventCreate(&e1));
       float best_ms = 1e30f;
       std::pair<int, int> best(0, 0);
+      bool all_dia = true;  // entry lanes do not apply to the diagonal-offset form
+      for (const SpmmArgs& a : args) all_dia = all_dia && a.ndiag > 0;
       for (int cm = 1; cm <= 2; ++cm)
-        for (int kl = 1; kl <= 16; kl *= 2) {
+        for (int kl = 1; kl <= (all_dia ? 1 : 16); kl *= 2) {
           std::vector<SpmmArgs> cand = args;
           for (SpmmArgs& a : cand) {
             a.cpt = V * cm;
@@ -334,7 +338,7 @@ static void add_coarse(Batch* B, std::vector<BLaunch>& plan, VecType vt, const s
 static void run_plan(const std::vector<BLaunch>& plan, cudaStream_t st) {
   for (const BLaunch& L : plan) {
     if (L.kind == 0)
-      launch_spmm_batch(L.mt, L.xt, L.ot, L.cpt, L.kl, L.dot, L.ifc, static_cast<const SpmmArgs*>(L.args), L.items,
+      launch_spmm_batch(L.mt, L.xt, L.ot, L.cpt, L.kl, L.dot, L.ifc, L.dia, static_cast<const SpmmArgs*>(L.args), L.items,
                         L.n_items, L.dots, L.smem, st);
     else if (L.kind == 1)
       launch_vec_batch(L.op, L.xt, L.cpt, static_cast<const UpdArgs*>(L.args), L.items, L.n_items, L.dots, L.smem,

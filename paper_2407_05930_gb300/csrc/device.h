@@ -30,6 +30,16 @@ struct DevCsr {
   const void* vals(ValType t) const {
     return t == VAL_F64 ? (const void*)v64 : t == VAL_F32 ? (const void*)v32 : (const void*)v16;
   }
+  // Diagonal-offset copy (ndiag > 0; layout and indexing as the host Dia):
+  // [nstored][rows] values per precision built.
+  int32_t ndiag = 0;
+  int32_t doff[kMaxDiag] = {}, dsrc[kMaxDiag] = {}, dshift[kMaxDiag] = {};
+  double* dv64 = nullptr;
+  float* dv32 = nullptr;
+  __nv_bfloat16* dv16 = nullptr;
+  const void* dvals(ValType t) const {
+    return t == VAL_F64 ? (const void*)dv64 : t == VAL_F32 ? (const void*)dv32 : (const void*)dv16;
+  }
 };
 
 // Interface couplings A_out,i of eq. "hL_splitting" in a form the SpMM can
@@ -119,6 +129,12 @@ struct SpmmArgs {
   // thread (0 = one 16-byte vector; 2x that when C allows); see spmm_kernel.
   int32_t kl = 0;
   int32_t cpt = 0;
+  // Diagonal-offset form (ndiag > 0 selects it; ptr/idx/val unused): the
+  // entry (row, row + doff[d]) exists when that column is in [0, rows) and
+  // has the value dval[dsrc[d] * rows + row + dshift[d]].
+  int32_t ndiag = 0;
+  int32_t doff[kMaxDiag] = {}, dsrc[kMaxDiag] = {}, dshift[kMaxDiag] = {};
+  const void* dval = nullptr;
   DotArgs dot;
 };
 
@@ -219,7 +235,7 @@ struct CoarseArgs {
 
 enum BatchVecOp { BOP_UPDATE1 = 0, BOP_UPDATE2 = 1, BOP_COPY = 2 };
 
-void launch_spmm_batch(ValType mt, VecType xt, VecType ot, int cpt, int kl, bool dot, bool iface,
+void launch_spmm_batch(ValType mt, VecType xt, VecType ot, int cpt, int kl, bool dot, bool iface, bool dia,
                        const SpmmArgs* args, const BItem* items, int32_t n_items, const BDot* dots,
                        size_t smem, cudaStream_t st);
 void launch_vec_batch(int op, VecType vt, int cpt, const UpdArgs* args, const BItem* items, int32_t n_items,

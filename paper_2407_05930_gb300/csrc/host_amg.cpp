@@ -598,6 +598,74 @@ void build_hierarchy(const Csr& A0, const amgsym_opts& o, HostHierarchy& H) {
   }
 }
 
+// Diagonal-offset form (see Dia): distinct column offsets counted with an
+// early exit, padding bounded, then exact symmetry checked diagonal by
+// diagonal so that a symmetric stencil stores only its lower half.
+Dia build_dia(const Csr& M, int max_diag) {
+  Dia D;
+  const int64_t n = M.rows;
+  if (max_diag <= 0 || n <= 0 || M.cols != n || n > INT32_MAX) return D;
+  max_diag = std::min(max_diag, kMaxDiag);
+  std::vector<int64_t> offs;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = M.ptr[i]; e < M.ptr[i + 1]; ++e) {
+      const int64_t o = (int64_t)M.idx[e] - i;
+      if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
+        if ((int)offs.size() == max_diag) return D;
+        offs.push_back(o);
+      }
+    }
+  if (offs.empty() || (double)offs.size() * (double)n > 1.25 * (double)M.nnz()) return D;
+  std::sort(offs.begin(), offs.end());
+  const int nd = (int)offs.size();
+  std::vector<double> full((size_t)nd * n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = M.ptr[i]; e < M.ptr[i + 1]; ++e) {
+      const int64_t o = (int64_t)M.idx[e] - i;
+      const int d = (int)(std::find(offs.begin(), offs.end(), o) - offs.begin());
+      full[(size_t)d * n + i] += M.val[e];
+    }
+  // exact symmetry: a_{i,i+o} == a_{i+o,i} for every upper diagonal o
+  bool sym = true;
+  for (int d = 0; d < nd && sym; ++d) {
+    if (offs[d] <= 0) continue;
+    const auto it = std::find(offs.begin(), offs.end(), -offs[d]);
+    if (it == offs.end()) {
+      sym = false;
+      break;
+    }
+    const int dl = (int)(it - offs.begin());
+    for (int64_t i = 0; i + offs[d] < n; ++i)
+      if (full[(size_t)d * n + i] != full[(size_t)dl * n + i + offs[d]]) {
+        sym = false;
+        break;
+      }
+  }
+  D.ndiag = nd;
+  std::vector<int> stored_of(nd, -1);
+  for (int d = 0; d < nd; ++d) {
+    D.off[d] = (int32_t)offs[d];
+    if (sym && offs[d] > 0) continue;
+    stored_of[d] = D.nstored++;
+  }
+  for (int d = 0; d < nd; ++d) {
+    if (stored_of[d] >= 0) {
+      D.src[d] = stored_of[d];
+      D.shift[d] = 0;
+    } else {
+      const int dl = (int)(std::find(offs.begin(), offs.end(), -offs[d]) - offs.begin());
+      D.src[d] = stored_of[dl];
+      D.shift[d] = (int32_t)offs[d];
+    }
+  }
+  D.val.resize((size_t)D.nstored * n);
+  for (int d = 0; d < nd; ++d)
+    if (stored_of[d] >= 0)
+      std::copy(full.begin() + (size_t)d * n, full.begin() + (size_t)(d + 1) * n,
+                D.val.begin() + (size_t)stored_of[d] * n);
+  return D;
+}
+
 }  // namespace amgsym
 
 using namespace amgsym;
@@ -630,6 +698,11 @@ extern "C" amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts) {
   h->have_hierarchy = false;
   h->opts = o;
   build_hierarchy(h->Ainn, o, h->H);
+  for (HostLevel& L : h->H.levels) {
+    L.Adia = build_dia(L.A, o.dia_max_diag);
+    L.Gdia = build_dia(L.G, o.dia_max_diag);
+    L.Gtdia = build_dia(L.Gt, o.dia_max_diag);
+  }
   h->have_hierarchy = true;
   if (!o.host_only) device_upload(h);
   API_END
@@ -669,5 +742,20 @@ extern "C" amgsym_status amgsym_get_level_matrix(amgsym_t h, int32_t level, int3
   std::memcpy(rowptr, M->ptr.data(), sizeof(int64_t) * M->ptr.size());
   std::memcpy(colidx, M->idx.data(), sizeof(int32_t) * M->idx.size());
   std::memcpy(vals, M->val.data(), sizeof(double) * M->val.size());
+  API_END
+}
+
+extern "C" amgsym_status amgsym_level_dia(amgsym_t h, int32_t level, int32_t which, int32_t* ndiag,
+                                         int32_t* nstored, int32_t* offsets) {
+  API_BEGIN
+  if (!h || !h->have_hierarchy) fail(AMGSYM_ERR_STATE, "no hierarchy (call amgsym_setup)");
+  if (level < 0 || level >= (int32_t)h->H.levels.size()) fail(AMGSYM_ERR_ARG, "level out of range");
+  const HostLevel& L = h->H.levels[level];
+  const Dia* D = which == 0 ? &L.Adia : which == 2 ? &L.Gdia : which == 3 ? &L.Gtdia : nullptr;
+  if (!D) fail(AMGSYM_ERR_ARG, "which must be 0 (A), 2 (G) or 3 (G^T)");
+  if (ndiag) *ndiag = D->ndiag;
+  if (nstored) *nstored = D->nstored;
+  if (offsets)
+    for (int d = 0; d < AMGSYM_MAX_DIAG; ++d) offsets[d] = d < D->ndiag ? D->off[d] : 0;
   API_END
 }

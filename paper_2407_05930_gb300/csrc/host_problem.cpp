@@ -59,6 +59,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->host_only = 0;
   o->seed = 12345;
   o->coarse_drop = 0.003;
+  o->dia_max_diag = AMGSYM_MAX_DIAG;
 }
 
 extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {

@@ -28,6 +28,23 @@ struct Error {
 [[noreturn]] void fail(amgsym_status code, const std::string& msg);
 void set_last_error(const std::string& msg);
 
+// Diagonal-offset form of a square matrix whose entries lie on a few
+// diagonals (the stencil of a structured grid and its FSAI factors):
+// diagonal d holds the entries (i, i + off[d]), offsets ascending, and its
+// value at row i is val[src[d] * rows + i + shift[d]].  shift[d] = off[d]
+// for an upper diagonal of an exactly symmetric matrix, read as the mirror
+// image of the stored lower diagonal src[d] (a_{i,i+o} = a_{i+o,i}); every
+// other diagonal is stored (shift 0).  Positions outside the pattern hold 0.
+constexpr int kMaxDiag = 8;
+struct Dia {
+  int32_t ndiag = 0, nstored = 0;
+  int32_t off[kMaxDiag] = {}, src[kMaxDiag] = {}, shift[kMaxDiag] = {};
+  std::vector<double> val;  // [nstored][rows]
+};
+// The diagonal-offset form of M when it is square, has at most max_diag
+// distinct column offsets and at most 25 % padding; else ndiag = 0.
+Dia build_dia(const Csr& M, int max_diag);
+
 // One level of the AMG hierarchy of A_inn (host copies).
 struct HostLevel {
   Csr A;        // level operator (level 0: A_inn)
@@ -35,6 +52,7 @@ struct HostLevel {
   Csr R;        // restriction P^T
   Csr G;        // FSAI factor, lower triangular (G^T G ~ A^{-1})
   Csr Gt;       // G^T
+  Dia Adia, Gdia, Gtdia;  // diagonal-offset forms (ndiag = 0: CSR only)
   double omega = 1.0;
   double lambda_max = 0.0;
   std::vector<double> coarse_inv;  // coarsest level: dense A^{-1}, row-major

@@ -17,7 +17,7 @@
 
 namespace amgsym {
 
-template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE>
+template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE, bool DIA>
 __global__ void __launch_bounds__(kBlock, 4)
     spmm_batch_kernel(const SpmmArgs* __restrict__ args, const BItem* __restrict__ items, int32_t n_items,
                       const BDot* __restrict__ dots) {
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kBlock, 4)
     DT dpart[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) dpart[q] = (DT)0;
-    spmm_tile<MT, XT, OT, CPT, KL, HAS_DOT, HAS_IFACE>(a, bi.first_slot, 1, bi.row_end, dpart);
+    spmm_tile<MT, XT, OT, CPT, KL, HAS_DOT, HAS_IFACE, DIA>(a, bi.first_slot, 1, bi.row_end, dpart);
     if (HAS_DOT) {
       const TileLayout t = tile_layout<CPT, KL>(a.C);
       double part[CPT];
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kBlock, 4)
   }
 }
 
-template <typename MT, typename XT, typename OT, int CPT, int KL>
+template <typename MT, typename XT, typename OT, int CPT, int KL, bool DIA = false>
 static void spmm_batch_k(bool dot, bool iface, const SpmmArgs* args, const BItem* items, int32_t n_items,
                          const BDot* dots, size_t smem, cudaStream_t st) {
   auto run = [&](auto kern) {
@@ -55,20 +55,25 @@ static void spmm_batch_k(bool dot, bool iface, const SpmmArgs* args, const BItem
   };
   if (dot) {
     if (iface)
-      run(spmm_batch_kernel<MT, XT, OT, CPT, KL, true, true>);
+      run(spmm_batch_kernel<MT, XT, OT, CPT, KL, true, true, DIA>);
     else
-      run(spmm_batch_kernel<MT, XT, OT, CPT, KL, true, false>);
+      run(spmm_batch_kernel<MT, XT, OT, CPT, KL, true, false, DIA>);
   } else {
     if (iface)
-      run(spmm_batch_kernel<MT, XT, OT, CPT, KL, false, true>);
+      run(spmm_batch_kernel<MT, XT, OT, CPT, KL, false, true, DIA>);
     else
-      run(spmm_batch_kernel<MT, XT, OT, CPT, KL, false, false>);
+      run(spmm_batch_kernel<MT, XT, OT, CPT, KL, false, false, DIA>);
   }
 }
 
+// dia: every record of the launch is in the diagonal-offset form (one lane per row)
 template <typename MT, typename XT, typename OT, int CPT>
-static void spmm_batch_c(int kl, bool dot, bool iface, const SpmmArgs* args, const BItem* items, int32_t n_items,
-                         const BDot* dots, size_t smem, cudaStream_t st) {
+static void spmm_batch_c(int kl, bool dot, bool iface, bool dia, const SpmmArgs* args, const BItem* items,
+                         int32_t n_items, const BDot* dots, size_t smem, cudaStream_t st) {
+  if (dia) {
+    spmm_batch_k<MT, XT, OT, CPT, 1, true>(dot, iface, args, items, n_items, dots, smem, st);
+    return;
+  }
   switch (kl) {
     case 1: spmm_batch_k<MT, XT, OT, CPT, 1>(dot, iface, args, items, n_items, dots, smem, st); break;
     case 2: spmm_batch_k<MT, XT, OT, CPT, 2>(dot, iface, args, items, n_items, dots, smem, st); break;
@@ -79,29 +84,31 @@ static void spmm_batch_c(int kl, bool dot, bool iface, const SpmmArgs* args, con
 }
 
 template <typename MT, typename XT, typename OT>
-static void spmm_batch_t(int cpt, int kl, bool dot, bool iface, const SpmmArgs* args, const BItem* items,
+static void spmm_batch_t(int cpt, int kl, bool dot, bool iface, bool dia, const SpmmArgs* args, const BItem* items,
                          int32_t n_items, const BDot* dots, size_t smem, cudaStream_t st) {
   switch (cpt) {
-    case 8: spmm_batch_c<MT, XT, OT, 8>(kl, dot, iface, args, items, n_items, dots, smem, st); break;
-    case 4: spmm_batch_c<MT, XT, OT, 4>(kl, dot, iface, args, items, n_items, dots, smem, st); break;
-    case 2: spmm_batch_c<MT, XT, OT, 2>(kl, dot, iface, args, items, n_items, dots, smem, st); break;
-    default: spmm_batch_c<MT, XT, OT, 1>(kl, dot, iface, args, items, n_items, dots, smem, st); break;
+    case 8: spmm_batch_c<MT, XT, OT, 8>(kl, dot, iface, dia, args, items, n_items, dots, smem, st); break;
+    case 4: spmm_batch_c<MT, XT, OT, 4>(kl, dot, iface, dia, args, items, n_items, dots, smem, st); break;
+    case 2: spmm_batch_c<MT, XT, OT, 2>(kl, dot, iface, dia, args, items, n_items, dots, smem, st); break;
+    default: spmm_batch_c<MT, XT, OT, 1>(kl, dot, iface, dia, args, items, n_items, dots, smem, st); break;
   }
 }
 
-void launch_spmm_batch(ValType mt, VecType xt, VecType ot, int cpt, int kl, bool dot, bool iface,
+void launch_spmm_batch(ValType mt, VecType xt, VecType ot, int cpt, int kl, bool dot, bool iface, bool dia,
                        const SpmmArgs* args, const BItem* items, int32_t n_items, const BDot* dots, size_t smem,
                        cudaStream_t st) {
   if (n_items <= 0) return;
   count_launch();
   if (mt == VAL_F32 && xt == VEC_F32 && ot == VEC_F32)
-    spmm_batch_t<float, float, float>(cpt, kl, dot, iface, args, items, n_items, dots, smem, st);
+    spmm_batch_t<float, float, float>(cpt, kl, dot, iface, dia, args, items, n_items, dots, smem, st);
   else if (mt == VAL_BF16 && xt == VEC_F32 && ot == VEC_F32)
-    spmm_batch_t<__nv_bfloat16, float, float>(cpt, kl, dot, iface, args, items, n_items, dots, smem, st);
+    spmm_batch_t<__nv_bfloat16, float, float>(cpt, kl, dot, iface, dia, args, items, n_items, dots, smem, st);
   else if (mt == VAL_F64 && xt == VEC_F64 && ot == VEC_F32)
-    spmm_batch_t<double, double, float>(cpt <= 2 ? cpt : 2, kl, dot, iface, args, items, n_items, dots, smem, st);
+    spmm_batch_t<double, double, float>(cpt <= 2 ? cpt : 2, kl, dot, iface, dia, args, items, n_items, dots, smem,
+                                        st);
   else if (mt == VAL_F64 && xt == VEC_F64 && ot == VEC_F64)
-    spmm_batch_t<double, double, double>(cpt <= 4 ? cpt : 4, kl, dot, iface, args, items, n_items, dots, smem, st);
+    spmm_batch_t<double, double, double>(cpt <= 4 ? cpt : 4, kl, dot, iface, dia, args, items, n_items, dots, smem,
+                                         st);
   else
     fail(AMGSYM_ERR_ARG, "unsupported batched SpMM precision combination");
 }

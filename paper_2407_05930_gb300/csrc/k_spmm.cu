@@ -17,6 +17,13 @@
 // (broadcast).  Rows are walked grid-stride so a wave of blocks touches a
 // contiguous window of rows (L2 reuse of the gathered X rows).
 //
+// Matrix storage: CSR, or the diagonal-offset form of a matrix whose
+// entries lie on a few diagonals (the structured-grid stencil A_inn of the
+// finest level and its FSAI factors): no row pointers or column indices are
+// read, the value streams and the gathered rows row + offset are contiguous
+// across a warp, and a symmetric matrix reads its upper diagonals as shifted
+// copies of the stored lower ones.
+//
 // Epilogue: Y = alpha * (M X) + beta * Z (Z read only when beta != 0), then
 // an optional per-column dot (W.Y or Y.Y) reduced deterministically.
 #include <cuda_bf16.h>
@@ -25,8 +32,8 @@
 
 namespace amgsym {
 
-template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE>
-__global__ void __launch_bounds__(kBlock, (CPT >= 8 ? 4 : (HAS_DOT || HAS_IFACE) ? 6 : 8)) spmm_kernel(SpmmArgs a) {
+template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE, bool DIA>
+__global__ void __launch_bounds__(kBlock, ((DIA || CPT >= 8) ? 4 : (HAS_DOT || HAS_IFACE) ? 6 : 8)) spmm_kernel(SpmmArgs a) {
   using DT = typename AccOf<XT>::type;
   if (a.skip && *a.skip == 0) return;  // uniform over the grid
   DT dpart[CPT];
@@ -35,7 +42,7 @@ __global__ void __launch_bounds__(kBlock, (CPT >= 8 ? 4 : (HAS_DOT || HAS_IFACE)
   // Grid-stride over row slots: a wave of blocks sweeps one contiguous window
   // of rows, so the far neighbours one block gathers were recently brought
   // into L2 by another.
-  spmm_tile<MT, XT, OT, CPT, KL, HAS_DOT, HAS_IFACE>(a, blockIdx.x, gridDim.x, a.rows, dpart);
+  spmm_tile<MT, XT, OT, CPT, KL, HAS_DOT, HAS_IFACE, DIA>(a, blockIdx.x, gridDim.x, a.rows, dpart);
   if (HAS_DOT) {
     const TileLayout t = tile_layout<CPT, KL>(a.C);
     extern __shared__ double sm[];
@@ -47,7 +54,7 @@ __global__ void __launch_bounds__(kBlock, (CPT >= 8 ? 4 : (HAS_DOT || HAS_IFACE)
   }
 }
 
-template <typename MT, typename XT, typename OT, int CPT, int KL>
+template <typename MT, typename XT, typename OT, int CPT, int KL, bool DIA = false>
 static void launch_k(const SpmmArgs& a, cudaStream_t st) {
   const int TPC = a.C / CPT;
   const int rows_pb = kBlock / (TPC * KL);
@@ -66,19 +73,23 @@ static void launch_k(const SpmmArgs& a, cudaStream_t st) {
   if (dot) {
     const size_t smem = sizeof(double) * (size_t)dot_smem_doubles(TPC * KL, rows_pb, a.C);
     if (ifc)
-      run(spmm_kernel<MT, XT, OT, CPT, KL, true, true>, smem);
+      run(spmm_kernel<MT, XT, OT, CPT, KL, true, true, DIA>, smem);
     else
-      run(spmm_kernel<MT, XT, OT, CPT, KL, true, false>, smem);
+      run(spmm_kernel<MT, XT, OT, CPT, KL, true, false, DIA>, smem);
   } else {
     if (ifc)
-      run(spmm_kernel<MT, XT, OT, CPT, KL, false, true>, 0);
+      run(spmm_kernel<MT, XT, OT, CPT, KL, false, true, DIA>, 0);
     else
-      run(spmm_kernel<MT, XT, OT, CPT, KL, false, false>, 0);
+      run(spmm_kernel<MT, XT, OT, CPT, KL, false, false, DIA>, 0);
   }
 }
 
 template <typename MT, typename XT, typename OT, int CPT>
 static void launch_t(const SpmmArgs& a, cudaStream_t st) {
+  if (a.ndiag > 0) {  // diagonal-offset form: one lane per row
+    launch_k<MT, XT, OT, CPT, 1, true>(a, st);
+    return;
+  }
   const int TPC = a.C / CPT;
   // entry lanes: only with a power-of-two column-thread count, and S <= 32
   int kl = a.kl > 0 ? a.kl : 1;

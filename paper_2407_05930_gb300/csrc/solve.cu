@@ -44,7 +44,7 @@ static T* upload(std::vector<void*>& owner, const T* src, int64_t count) {
   return d;
 }
 
-static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions) {
+static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions, const Dia* dia = nullptr) {
   DevCsr D;
   if (M.rows > INT32_MAX || M.nnz() > INT32_MAX) fail(AMGSYM_ERR_ARG, "matrix too large for 32-bit device indices");
   D.rows = (int32_t)M.rows;
@@ -63,6 +63,27 @@ static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions
     std::vector<__nv_bfloat16> v(D.nnz);
     for (int64_t i = 0; i < D.nnz; ++i) v[i] = __float2bfloat16((float)M.val[i]);
     D.v16 = upload(owner, v.data(), D.nnz);
+  }
+  if (dia && dia->ndiag > 0) {
+    // the same value conversions as the CSR copies, so both forms multiply
+    // by identical numbers
+    D.ndiag = dia->ndiag;
+    for (int d = 0; d < kMaxDiag; ++d) {
+      D.doff[d] = dia->off[d];
+      D.dsrc[d] = dia->src[d];
+      D.dshift[d] = dia->shift[d];
+    }
+    const int64_t cnt = (int64_t)dia->val.size();
+    if (precisions & 1) D.dv64 = upload(owner, dia->val.data(), cnt);
+    if (precisions & 2) {
+      std::vector<float> v(dia->val.begin(), dia->val.end());
+      D.dv32 = upload(owner, v.data(), cnt);
+    }
+    if (precisions & 4) {
+      std::vector<__nv_bfloat16> v(cnt);
+      for (int64_t i = 0; i < cnt; ++i) v[i] = __float2bfloat16((float)dia->val[i]);
+      D.dv16 = upload(owner, v.data(), cnt);
+    }
   }
   return D;
 }
@@ -115,14 +136,14 @@ void device_upload(amgsym_problem* p) {
     V.n = (int32_t)L.A.rows;
     V.omega = L.omega;
     // level 0 keeps FP64 always (the reduced operator of the outer loop)
-    V.A = upload_csr(D->owned, L.A, l == 0 ? D->precisions : p->opts.precisions);
+    V.A = upload_csr(D->owned, L.A, l == 0 ? D->precisions : p->opts.precisions, &L.Adia);
     if (!L.coarse_inv.empty()) {
       V.cinv = upload(D->owned, L.coarse_inv.data(), (int64_t)L.coarse_inv.size());
     } else {
       V.P = upload_csr(D->owned, L.P, p->opts.precisions);
       V.R = upload_csr(D->owned, L.R, p->opts.precisions);
-      V.G = upload_csr(D->owned, L.G, p->opts.precisions);
-      V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions);
+      V.G = upload_csr(D->owned, L.G, p->opts.precisions, &L.Gdia);
+      V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions, &L.Gtdia);
     }
   }
   D->Ainn = D->lv[0].A;
@@ -236,7 +257,10 @@ Tile fixed_tile(const DevCsr& M, int32_t C, VecType xt) {
   const bool two = C % (2 * V) == 0 && C / (2 * V) >= 1;
   Tile t;
   const double r = M.avg_row;
-  if (r < 10.0) {
+  if (M.ndiag > 0) {  // diagonal-offset form: one lane per row, two vectors
+    t.cpt = two ? 2 * V : V;
+    t.kl = 1;
+  } else if (r < 10.0) {
     t.cpt = two ? 2 * V : V;
     t.kl = 1;
   } else if (r < 32.0) {
@@ -280,6 +304,15 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
     const bool f64 = (mt == VAL_F64) || (xt == VEC_F64);
     a.ival = f64 ? (const void*)c.D->iface.ival64 : (const void*)c.D->iface.ival32;
     a.nb = c.D->nb;
+  }
+  if (M.ndiag > 0 && M.dvals(mt)) {
+    a.ndiag = M.ndiag;
+    for (int d = 0; d < kMaxDiag; ++d) {
+      a.doff[d] = M.doff[d];
+      a.dsrc[d] = M.dsrc[d];
+      a.dshift[d] = M.dshift[d];
+    }
+    a.dval = M.dvals(mt);
   }
   if (dot) a.dot = *dot;
   a.skip = c.skip;
@@ -353,7 +386,7 @@ void tune_tiles(const Ctx& c) {
       if (c.C % cpt) continue;
       const int tpc = c.C / cpt;
       for (int kl = 1; kl <= 16; kl *= 2) {
-        if (kl > 1 && ((tpc & (tpc - 1)) || tpc * kl > 32)) break;
+        if (kl > 1 && ((tpc & (tpc - 1)) || tpc * kl > 32 || j.M->ndiag > 0)) break;
         Ctx cc = c;
         D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)c.vt}] = Tile{cpt, kl};
         spmm(cc, *j.M, j.mt, c.vt, c.vt, j.X, j.Y, 1.0, 0.0, nullptr, j.iface, nullptr);  // warm-up

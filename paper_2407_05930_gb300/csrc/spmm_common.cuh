@@ -77,6 +77,46 @@ struct ComputeOf<double, double> {
   using type = double;
 };
 
+// The entries of one row in the diagonal-offset form: every value load and
+// gather of a batch of diagonals issued before its FMAs (no dependent index
+// loads: the columns are row + offset); one batch holds all diagonals with
+// 16-byte column vectors and four with 32-byte ones (registers).  The sum
+// runs over the diagonals in ascending offset, i.e. column, order -- the
+// order of the CSR loop -- and skips columns outside [0, rows); padded
+// positions inside hold 0 and add fma(0, x, acc) = acc.
+template <typename MT, typename XT, typename CT, int CPT>
+__device__ __forceinline__ void dia_row(const SpmmArgs& a, int row, int c0, CT (&acc)[CPT]) {
+  const MT* __restrict__ dv = static_cast<const MT*>(a.dval);
+  const XT* __restrict__ X = static_cast<const XT*>(a.X);
+  const int64_t n = a.rows;
+  constexpr int UB = CPT * sizeof(XT) >= 32 ? 4 : kMaxDiag;
+#pragma unroll
+  for (int d0 = 0; d0 < kMaxDiag; d0 += UB) {
+    if (d0 < a.ndiag) {
+      CT m[UB];
+      Vec<XT, CPT> x[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        const int d = d0 + u;
+        const int j = row + a.doff[d];
+        const bool ok = d < a.ndiag && (unsigned)j < (unsigned)a.rows;
+        m[u] = ok ? cvt<CT>(dv[(int64_t)a.dsrc[d] * n + row + a.dshift[d]]) : (CT)0;
+        if (ok) {
+          x[u] = ldv<XT, CPT>(X + (int64_t)j * a.C + c0);
+        } else {
+#pragma unroll
+          for (int q = 0; q < CPT; ++q) x[u].v[q] = (XT)0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) acc[q] = fma(m[u], (CT)x[u].v[q], acc[q]);
+      }
+    }
+  }
+}
+
 // Rows [first_slot * rows_pb + k * slot_step * rows_pb, ...) below row_end
 // of one SpMM, for the whole block; this thread's dot partial (entry lane 0
 // only) is added to dpart.  Thread layout: a row is served by S = TPC * KL
@@ -85,15 +125,18 @@ struct ComputeOf<double, double> {
 // ...).  The KL partial sums are combined with warp shuffles (S divides 32
 // when KL > 1), and entry lane 0 runs the epilogue.  KL > 1 keeps several
 // gathers of one row in flight (the ptr -> idx -> X latency chain) and spreads
-// the long rows of the coarse levels over many lanes.
-template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE>
+// the long rows of the coarse levels over many lanes.  DIA: the matrix is in
+// the diagonal-offset form (one lane per row, no row pointers).
+template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE, bool DIA = false>
 __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int slot_step, int row_end,
                                           typename AccOf<XT>::type (&dpart)[CPT]) {
+  static_assert(!DIA || KL == 1, "the diagonal-offset form runs one entry lane per row");
   using CT = typename ComputeOf<MT, XT>::type;
   using DT = typename AccOf<XT>::type;  // per-thread dot partial type
   // Early epilogue-operand load only where the register budget allows it
   // without spills (the variants launched at 6 blocks per SM).
   constexpr bool ZPF = HAS_DOT || HAS_IFACE;
+  constexpr bool PTR_PF = ZPF && !DIA;
   const int C = a.C;
   const int TPC = C / CPT;
   const int S = TPC * KL;
@@ -118,7 +161,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
   // dependent load off each row's chain.
   const int step_rows = slot_step * rows_pb;
   int kb_next = 0, ke_next = 0;
-  if (ZPF) {
+  if (PTR_PF) {
     const int row0 = first_slot * rows_pb + g;
     if (slot_ok && row0 < row_end) {
       kb_next = __ldg(ptr + row0);
@@ -133,12 +176,12 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
     for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
     Vec<XT, CPT> zpre;
     int kb = kb_next, ke = ke_next;
-    if (ZPF) {
+    if (PTR_PF) {
       if (slot_ok && row + step_rows < row_end) {
         kb_next = __ldg(ptr + row + step_rows);
         ke_next = __ldg(ptr + row + step_rows + 1);
       }
-    } else if (live) {
+    } else if (!DIA && live) {
       kb = __ldg(ptr + row);
       ke = __ldg(ptr + row + 1);
     }
@@ -147,7 +190,8 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
       // off the critical path of the gathers
       const uint32_t iface_word = (HAS_IFACE && e == 0) ? __ldg(a.imask + (row >> 5)) : 0u;
       if (ZPF && e == 0 && a.beta != 0.0) zpre = ldv<XT, CPT>(Z + (int64_t)row * C + c0);
-      int k = kb + e;
+      if (DIA) dia_row<MT, XT, CT, CPT>(a, row, c0, acc);
+      int k = DIA ? ke : kb + e;  // the diagonal form has no CSR entries
       // U entries per step, predicated: all index/value loads first, then all
       // gathers, so a row of up to U * KL entries costs one round trip and a
       // 7-point row (U = 4) two, with every gather of a step in flight at once

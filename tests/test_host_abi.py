@@ -176,3 +176,39 @@ def test_hierarchy_structure(drop):
         inf = P.level_info(l)
         assert 0.0 < inf["omega"] < 2.0
     assert P.level_info(L - 1)["rows"] <= 128
+
+
+@pytest.mark.parametrize("N,s", [((12, 10, 8), 3), ((64, 64), 1), ((10, 8, 6), 0)])
+def test_diagonal_form_detection(N, s):
+    """The diagonal-offset copies of the structured-grid operators: the base
+    block of a d-dimensional stencil has the 2d+1 offsets 0, +-1, +-nx,
+    +-nx*ny (x fastest), stores its lower half only (exactly symmetric
+    finite-volume matrix); its FSAI factor G has the lower offsets and G^T
+    the upper ones, all stored; no diagonal form above AMGSYM_MAX_DIAG or
+    with dia_max_diag = 0."""
+    g = gaussian_logk(N, s, seed=4, corr=2.0)
+    P = amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, coarse_max=32)
+    base = list(N)
+    for a in range(s):
+        base[a] //= 2
+    strides = [int(np.prod(base[:a])) for a in range(len(base))]
+    lower = sorted([-t for t in strides] + [0])
+    full = sorted(set(lower + [t for t in strides]))
+    A = P.level_dia(0, "A")
+    assert A["offsets"] == full and A["ndiag"] == 2 * len(N) + 1
+    assert A["nstored"] == len(N) + 1
+    G, Gt = P.level_dia(0, "G"), P.level_dia(0, "Gt")
+    assert G["offsets"] == lower and G["nstored"] == G["ndiag"]
+    assert Gt["offsets"] == sorted(-o for o in lower) and Gt["nstored"] == Gt["ndiag"]
+    # the stored diagonal form reproduces the CSR matrix: checked on the GPU
+    # (bit-identical products); here its pattern must cover every entry
+    rp, ci, v, shape = P.level_matrix(0, "A")
+    rows = np.repeat(np.arange(shape[0]), np.diff(rp))
+    assert set(np.unique(ci - rows).tolist()) <= set(full)
+    Q = amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, coarse_max=32, dia_max_diag=0)
+    assert Q.level_dia(0, "A")["ndiag"] == 0 and Q.level_dia(0, "G")["ndiag"] == 0
+    R = amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, coarse_max=32, dia_max_diag=len(N) * 2)
+    assert R.level_dia(0, "A")["ndiag"] == 0 and R.level_dia(0, "G")["ndiag"] == len(N) + 1
+    assert amg.lib.amgsym_level_dia(P._h, 0, 1, None, None, None) == -1  # P has no diagonal form
+    with pytest.raises(amg.AmgsymError):
+        P.level_dia(P.num_levels(), "A")
