@@ -103,6 +103,14 @@ typedef struct {
                                exactly symmetric one stores its lower half only.  The sums
                                run in the CSR order, so results are bit-identical to the
                                CSR kernels.  0 = CSR only; default 8 = AMGSYM_MAX_DIAG */
+  int32_t fuse_rows;        /* the V-cycle from the first level below the finest with at
+                               most this many rows down to the coarsest solve runs as one
+                               persistent cooperative kernel (grid barriers between its
+                               products, the same tile code and summation order as one
+                               launch per product); 0 = one launch per product.  Not used
+                               by amgsym_vcycle_noalloc nor the batched solve.  Default 0:
+                               on GB300 a grid barrier costs about what a kernel node of
+                               the captured PCG iteration costs, so fusing gained nothing */
 } amgsym_opts;
 
 #define AMGSYM_MAX_DIAG 8
@@ -248,9 +256,23 @@ amgsym_status amgsym_apply_reduced(amgsym_t h, const void* X_dev, void* Y_dev, i
 /* Preconditioner (eqs. "AMGinn", "LRCAMG" with k = 0): Z = (I (x) M_inn^{-1}) R,
  * one symmetric V(nu, nu) cycle of the A_inn hierarchy applied to every
  * column; with finest_hat = 1 the finest-level residuals use A^_i.
- * R, Z: [n_b][nrhs*2^s], double (FP64) or float (mixed); must not overlap. */
+ * R, Z: [n_b][nrhs*2^s], double (FP64) or float (mixed); must not overlap.
+ * The levels from opts->fuse_rows down run as one persistent kernel; a
+ * timed-out barrier wait there (never in a correct run) is reported by the
+ * next amgsym_solve on the handle. */
 amgsym_status amgsym_vcycle(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs,
                             int32_t prec, int32_t finest_hat, void* stream);
+
+/* Failure check of the persistent coarse-cycle kernel (opts->fuse_rows): runs
+ * it once on the library's level work arrays with a grid barrier that awaits
+ * one arrival more than the grid has, so nothing releases it, and a wait bound
+ * of 4096 polls (a few milliseconds).  Every block's wait runs out, sets the
+ * error word and returns; the call synchronises the stream, reads the word and
+ * clears the barrier.  Returns AMGSYM_OK when the timed-out wait was reported
+ * (the handle stays usable), AMGSYM_ERR_CUDA when it was not or the launch
+ * failed, AMGSYM_ERR_STATE when the problem has no fused coarse cycle.  No
+ * counterpart in the paper: it tests this library's own bounded waits. */
+amgsym_status amgsym_cycle_timeout_check(amgsym_t h, int32_t nrhs, int32_t prec, void* stream);
 
 /* Preconditioner without allocation: the V-cycle of amgsym_vcycle (same
  * arguments, same kernels, same result), for callers that cannot let the

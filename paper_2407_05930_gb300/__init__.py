@@ -62,6 +62,7 @@ class Opts(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("coarse_drop", ctypes.c_double),
         ("dia_max_diag", ctypes.c_int32),
+        ("fuse_rows", ctypes.c_int32),
     ]
 
 
@@ -113,6 +114,7 @@ def _load():
         "amgsym_level_sizes": (i32, [P, i32, pi64, pi64, pi64, pi64, pi64, pdbl]),
         "amgsym_get_level_matrix": (i32, [P, i32, i32, pi64, pi32, pdbl]),
         "amgsym_level_dia": (i32, [P, i32, i32, pi32, pi32, pi32]),
+        "amgsym_cycle_timeout_check": (i32, [P, i32, i32, P]),
         "amgsym_solve": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
         "amgsym_solve_adjoint": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
         "amgsym_transform_forward": (i32, [P, P, i32, i64, P, P]),
@@ -152,7 +154,8 @@ EXPORTED = [
         "amgsym_solve_adjoint amgsym_transform_forward amgsym_transform_backward "
         "amgsym_apply_reduced amgsym_vcycle amgsym_vcycle_noalloc amgsym_grid_widths amgsym_fv_nnz "
         "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy "
-        "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles amgsym_level_dia"
+        "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles amgsym_level_dia "
+        "amgsym_cycle_timeout_check"
     ).split()
 ]
 
@@ -418,6 +421,11 @@ class Problem:
         _check(lib.amgsym_vcycle_noalloc(self._h, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()),
                                          nrhs, prec, 1 if finest_hat else 0, self._stream()))
         return Z
+
+    def cycle_timeout_check(self, nrhs: int = 1, prec: int = PREC_MIXED_FP32):
+        """Run the persistent coarse-cycle kernel with a barrier nothing releases
+        (see amgsym_cycle_timeout_check); raises unless the timeout was reported."""
+        _check(lib.amgsym_cycle_timeout_check(self._h, nrhs, prec, self._stream()))
 
     def vcycle(self, R, Z, nrhs: int, prec: int = PREC_FP64, finest_hat: bool = False):
         _check(lib.amgsym_vcycle(self._h, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()), nrhs, prec,

@@ -140,6 +140,8 @@ struct SpmmArgs {
 
 // Launchers (k_spmm.cu).  mt: matrix values, xt: X/Z/W vectors, ot: Y.
 void launch_spmm(ValType mt, VecType xt, VecType ot, const SpmmArgs& a, cudaStream_t st);
+// The (columns per thread, entry lanes) launch_spmm runs for these arguments.
+void spmm_resolved_tile(VecType xt, VecType ot, const SpmmArgs& a, int* cpt, int* kl);
 
 // Elementwise / transform / small kernels (k_misc.cu).
 void launch_transform_fwd(const double* b, int32_t nrhs, int64_t ld, const int32_t* perm, int64_t n_b,
@@ -234,6 +236,31 @@ struct CoarseArgs {
 };
 
 enum BatchVecOp { BOP_UPDATE1 = 0, BOP_UPDATE2 = 1, BOP_COPY = 2 };
+
+// ---------------------------------------------------------------------------
+// Persistent coarse-cycle kernel (k_cycle.cu): the phases of the V-cycle over
+// the coarsest levels, one cooperative launch, grid barriers between phases.
+enum CycleKind { CYCLE_SPMM = 0, CYCLE_DENSE = 1 };
+struct CyclePhase {
+  int32_t kind = CYCLE_SPMM;
+  SpmmArgs a;    // CYCLE_SPMM (no dot, no interface; a.kl = entry lanes)
+  CoarseArgs c;  // CYCLE_DENSE
+};
+// Grid barrier words (device): arrivals, generation, error flag (1 = a wait
+// ran out; the launch stopped early).
+struct CycleBar {
+  unsigned* count = nullptr;
+  unsigned* gen = nullptr;
+  int32_t* err = nullptr;
+  unsigned extra = 0;                // arrivals awaited beyond the grid (0; 1 only in the timeout check)
+  long long spins = 1ll << 22;       // polls (32 ns back-off each) before a wait gives up
+};
+// Columns per thread of the kernel for a column count, and its cooperative
+// grid (one block per SM; 0 = unavailable).
+int cycle_cpt(VecType vt, int32_t C);
+int cycle_grid(ValType mt, VecType vt, int32_t C);
+cudaError_t launch_cycle(ValType mt, VecType vt, int32_t C, int grid, const CyclePhase* phases, int32_t nphases,
+                         const CycleBar& bar, const int32_t* skip, cudaStream_t st);
 
 void launch_spmm_batch(ValType mt, VecType xt, VecType ot, int cpt, int kl, bool dot, bool iface, bool dia,
                        const SpmmArgs* args, const BItem* items, int32_t n_items, const BDot* dots,

@@ -690,6 +690,7 @@ extern "C" amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts) {
   amgsym_opts_default(&o);
   if (opts) o = *opts;
   if (o.nu < 1 || o.nu > 8) fail(AMGSYM_ERR_ARG, "nu must be in [1, 8]");
+  if (o.fuse_rows < 0 || o.dia_max_diag < 0) fail(AMGSYM_ERR_ARG, "fuse_rows and dia_max_diag must be >= 0");
   if (o.fsai_max_lower < 1 || o.fsai_max_lower > 32) fail(AMGSYM_ERR_ARG, "fsai_max_lower must be in [1, 32]");
   if (o.coarse_max < 1 || o.coarse_max > kDenseLimit) fail(AMGSYM_ERR_ARG, "coarse_max out of range");
   if (o.max_levels < 1) fail(AMGSYM_ERR_ARG, "max_levels must be >= 1");

@@ -60,6 +60,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->seed = 12345;
   o->coarse_drop = 0.003;
   o->dia_max_diag = AMGSYM_MAX_DIAG;
+  o->fuse_rows = 0;
 }
 
 extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {

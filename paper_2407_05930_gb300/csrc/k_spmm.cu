@@ -121,6 +121,32 @@ static void launch_c(const SpmmArgs& a, cudaStream_t st) {
     launch_t<MT, XT, OT, 1>(a, st);
 }
 
+void spmm_resolved_tile(VecType xt, VecType ot, const SpmmArgs& a, int* cpt, int* kl) {
+  // the choices of launch_c and launch_t
+  const int V = std::min(16 / (xt == VEC_F64 ? 8 : 4), 16 / (ot == VEC_F64 ? 8 : 4));
+  const int want = a.cpt > 0 ? a.cpt : V;
+  int c;
+  if (want >= 2 * V && V == 4 && a.C % 8 == 0 && a.C / 8 <= kBlock)
+    c = 8;
+  else if (want >= 2 * V && V == 2 && a.C % 4 == 0 && a.C / 4 <= kBlock)
+    c = 4;
+  else if (V >= 4 && a.C % 4 == 0 && a.C / 4 <= kBlock)
+    c = 4;
+  else if (V >= 2 && a.C % 2 == 0 && a.C / 2 <= kBlock)
+    c = 2;
+  else
+    c = 1;
+  int k = 1;
+  if (a.ndiag <= 0) {
+    const int tpc = a.C / c;
+    k = a.kl > 0 ? a.kl : 1;
+    if (tpc & (tpc - 1)) k = 1;
+    while (k > 1 && tpc * k > 32) k >>= 1;
+  }
+  *cpt = c;
+  *kl = k;
+}
+
 void launch_spmm(ValType mt, VecType xt, VecType ot, const SpmmArgs& a, cudaStream_t st) {
   if (a.rows <= 0) return;
   if (mt == VAL_F64 && xt == VEC_F64 && ot == VEC_F64)

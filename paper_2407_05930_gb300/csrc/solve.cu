@@ -100,6 +100,7 @@ static void free_work(Device* D) {
   D->work_nrhs = 0;
   if (D->graph.exec) cudaGraphExecDestroy(D->graph.exec);
   D->graph = GraphCache();
+  D->cycle_plans.clear();  // their phase arrays were work allocations
 }
 
 void device_free(amgsym_problem* p) {
@@ -175,6 +176,22 @@ void device_upload(amgsym_problem* p) {
     D->iface.ival64 = upload(D->owned, p->ivals.data(), ne * p->nb);
     std::vector<float> v32(p->ivals.begin(), p->ivals.end());
     D->iface.ival32 = upload(D->owned, v32.data(), ne * p->nb);
+  }
+  // persistent coarse cycle from the first level below the finest with at
+  // most fuse_rows rows (only when it leaves at least one product to fuse)
+  D->fuse_level = -1;
+  if (p->opts.fuse_rows > 0)
+    for (size_t l = 1; l < D->lv.size(); ++l)
+      if (D->lv[l].n <= p->opts.fuse_rows) {
+        if (!D->lv[l].cinv) D->fuse_level = (int)l;
+        break;
+      }
+  {
+    unsigned* words = dalloc<unsigned>(D->owned, 4);
+    CK(cudaMemset(words, 0, 4 * sizeof(unsigned)));
+    D->bar.count = words;
+    D->bar.gen = words + 1;
+    D->bar.err = reinterpret_cast<int32_t*>(words + 2);
   }
   CK(cudaStreamCreateWithFlags(&D->cap_stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&D->ev[0], cudaEventDisableTiming));
@@ -412,6 +429,126 @@ void tune_tiles(const Ctx& c) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   D->tuned.insert(key);
+  D->tiles_gen++;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent coarse cycle (k_cycle.cu).  The phases are the products of
+// vcycle() below from level Device::fuse_level down, in the same order with
+// the same arguments, entry lanes and therefore the same sums.
+
+static void cycle_phase(const Ctx& c, std::vector<CyclePhase>& out, const DevCsr& M, const void* X, void* Y,
+                        double alpha, double beta, const void* Z, int kcpt) {
+  CyclePhase ph;
+  ph.kind = CYCLE_SPMM;
+  ph.a = make_spmm_args(c, M, c.mt, c.vt, c.vt, X, Y, alpha, beta, Z, false, nullptr);
+  ph.a.skip = nullptr;
+  int cpt = 0, kl = 1;
+  spmm_resolved_tile(c.vt, c.vt, ph.a, &cpt, &kl);
+  // the kernel's own column split; entry lanes as the stand-alone launch
+  const int tpc = c.C / kcpt;
+  if (tpc & (tpc - 1)) kl = 1;
+  while (kl > 1 && tpc * kl > 32) kl >>= 1;
+  ph.a.kl = kl;
+  ph.a.cpt = kcpt;
+  out.push_back(ph);
+}
+
+static void cycle_phases(const Ctx& c, int l, const void* y, void* z, int kcpt, std::vector<CyclePhase>& out) {
+  Device* D = c.D;
+  const DevLevel& L = D->lv[l];
+  PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
+  LevelWork& lw = W.lw[l];
+  if (L.cinv) {
+    CyclePhase ph;
+    ph.kind = CYCLE_DENSE;
+    ph.c.n = L.n;
+    ph.c.C = c.C;
+    ph.c.Ainv = L.cinv;
+    ph.c.Y = y;
+    ph.c.Z = z;
+    out.push_back(ph);
+    return;
+  }
+  cycle_phase(c, out, L.G, y, lw.t, 1.0, 0.0, nullptr, kcpt);
+  cycle_phase(c, out, L.Gt, lw.t, z, L.omega, 0.0, nullptr, kcpt);
+  for (int k = 1; k < D->nu; ++k) {
+    cycle_phase(c, out, L.A, z, lw.r, -1.0, 1.0, y, kcpt);
+    cycle_phase(c, out, L.G, lw.r, lw.t, 1.0, 0.0, nullptr, kcpt);
+    cycle_phase(c, out, L.Gt, lw.t, z, L.omega, 1.0, z, kcpt);
+  }
+  cycle_phase(c, out, L.A, z, lw.r, -1.0, 1.0, y, kcpt);
+  LevelWork& cw = W.lw[l + 1];
+  cycle_phase(c, out, L.R, lw.r, cw.y, 1.0, 0.0, nullptr, kcpt);
+  cycle_phases(c, l + 1, cw.y, cw.z, kcpt, out);
+  cycle_phase(c, out, L.P, cw.z, z, 1.0, 1.0, z, kcpt);
+  for (int k = 0; k < D->nu; ++k) {
+    cycle_phase(c, out, L.A, z, lw.r, -1.0, 1.0, y, kcpt);
+    cycle_phase(c, out, L.G, lw.r, lw.t, 1.0, 0.0, nullptr, kcpt);
+    cycle_phase(c, out, L.Gt, lw.t, z, L.omega, 1.0, z, kcpt);
+  }
+}
+
+static CycleKey cycle_key(const Ctx& c) {
+  return CycleKey{c.C, (int)c.vt, (int)c.mt, c.D->work_gen, c.D->tiles_gen};
+}
+
+// Whether a cooperative launch works here and can be captured in a graph:
+// one capture of an empty launch (no phases: the kernel returns at once).
+static bool coop_supported(Device* D, const Ctx& c) {
+  if (D->coop_ok >= 0) return D->coop_ok == 1;
+  D->coop_ok = 0;
+  const int grid = cycle_grid(c.mt, c.vt, c.C);
+  if (grid < 1) return false;
+  int attr = 0;
+  if (cudaDeviceGetAttribute(&attr, cudaDevAttrCooperativeLaunch, D->device_id) != cudaSuccess || !attr) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  bool ok = cudaStreamBeginCapture(D->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const cudaError_t le = launch_cycle(c.mt, c.vt, c.C, grid, nullptr, 0, D->bar, nullptr, D->cap_stream);
+    count_launch(-1);
+    const cudaError_t ee = cudaStreamEndCapture(D->cap_stream, &g);
+    ok = le == cudaSuccess && ee == cudaSuccess && g != nullptr;
+    if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  (void)cudaGetLastError();
+  D->coop_ok = ok ? 1 : 0;
+  return ok;
+}
+
+void prepare_cycle(const Ctx& c) {
+  Device* D = c.D;
+  if (!c.fuse || D->fuse_level < 1) return;
+  const CycleKey key = cycle_key(c);
+  if (D->cycle_plans.count(key)) return;
+  if (!coop_supported(D, c)) return;
+  std::vector<CyclePhase> ph;
+  PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
+  const int l = D->fuse_level;
+  cycle_phases(c, l, W.lw[l].y, W.lw[l].z, cycle_cpt(c.vt, c.C), ph);
+  CyclePlan plan;
+  plan.grid = cycle_grid(c.mt, c.vt, c.C);
+  plan.nphases = (int32_t)ph.size();
+  plan.phases = dalloc<CyclePhase>(D->work_owned, plan.nphases);
+  CK(cudaMemcpy(plan.phases, ph.data(), sizeof(CyclePhase) * ph.size(), cudaMemcpyHostToDevice));
+  D->cycle_plans[key] = plan;
+}
+
+void check_cycle_error(Device* D, cudaStream_t st) {
+  if (D->fuse_level < 1 || D->cycle_plans.empty()) return;
+  int32_t err = 0;
+  CK(cudaMemcpyAsync(&err, D->bar.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (err) {
+    CK(cudaMemset(D->bar.count, 0, 4 * sizeof(unsigned)));
+    fail(AMGSYM_ERR_CUDA, "coarse-cycle kernel: a grid-barrier wait ran out (the launch stopped early)");
+  }
 }
 
 // One V(nu, nu) cycle at level l: z = M_l^{-1} y (Alg. "apply" shape with the
@@ -422,6 +559,15 @@ static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* l
   const DevLevel& L = D->lv[l];
   PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
   LevelWork& lw = W.lw[l];
+  if (c.fuse && l == D->fuse_level && !last) {
+    auto it = D->cycle_plans.find(cycle_key(c));
+    if (it != D->cycle_plans.end()) {
+      const CyclePlan& pl = it->second;
+      const cudaError_t e = launch_cycle(c.mt, c.vt, c.C, pl.grid, pl.phases, pl.nphases, D->bar, c.skip, c.st);
+      if (e != cudaSuccess) fail(AMGSYM_ERR_CUDA, std::string("coarse-cycle launch: ") + cudaGetErrorString(e));
+      return;
+    }
+  }
   if (L.cinv) {
     launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st, c.skip);
     check_launch();
@@ -501,11 +647,13 @@ static int pcg_loop(const Ctx& c0, PrecWork& W, const DevScalars& sc, int32_t nr
                     bool use_graph, int graph_mode, bool* breakdown) {
   Device* D = c0.D;
   if (c0.tune) tune_tiles(c0);
+  prepare_cycle(c0);
   Ctx c = c0;
   c.skip = sc.status;
   GraphKey graph_key;
   graph_key.mode = graph_mode;
   graph_key.nrhs = nrhs;
+  graph_key.tiles_gen = D->tiles_gen;
   // start: z = M r, rz, p = z
   DotArgs drz = make_dot(sc, DOT_WY, FIN_STORE_RZ, W.r, nrhs, D->nb, tol, 0);
   vcycle(c, 0, W.r, W.z, &drz);
@@ -568,6 +716,7 @@ static int pcg_loop(const Ctx& c0, PrecWork& W, const DevScalars& sc, int32_t nr
     if (!check(it - 1)) done_at = maxit;
   }
   CK(cudaStreamSynchronize(c.st));
+  check_cycle_error(D, c.st);
   return done_at < 0 ? maxit : done_at;
 }
 
@@ -605,6 +754,7 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
   const int32_t C = nrhs * D->nb;
   Ctx c{D, C, vt, vmt, o.finest_hat != 0, st};
   c.tune = o.tune != 0;
+  c.fuse = true;
   Ctx c64{D, C, VEC_F64, VAL_F64, false, st};
   // 64-bit work is needed for the FP64 path; the mixed path uses bh/xh only.
   PrecWork& W = mixed ? D->w32 : D->w64;
@@ -792,7 +942,37 @@ extern "C" amgsym_status amgsym_vcycle(amgsym_t h, const void* R_dev, void* Z_de
   const ValType mt = f64 ? VAL_F64 : prec == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : VAL_F32;
   ensure_work(D, nrhs, vt);
   Ctx c{D, nrhs * D->nb, vt, mt, finest_hat != 0, (cudaStream_t)stream};
+  c.fuse = true;
+  prepare_cycle(c);
   vcycle(c, 0, R_dev, Z_dev, nullptr);
+  API_END
+}
+
+extern "C" amgsym_status amgsym_cycle_timeout_check(amgsym_t h, int32_t nrhs, int32_t prec, void* stream) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (nrhs < 1 || (int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
+  const bool f64 = prec == AMGSYM_PREC_FP64;
+  const VecType vt = f64 ? VEC_F64 : VEC_F32;
+  const ValType mt = f64 ? VAL_F64 : prec == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : VAL_F32;
+  ensure_work(D, nrhs, vt);
+  Ctx c{D, nrhs * D->nb, vt, mt, false, (cudaStream_t)stream};
+  c.fuse = true;
+  prepare_cycle(c);
+  auto it = D->cycle_plans.find(cycle_key(c));
+  if (it == D->cycle_plans.end()) fail(AMGSYM_ERR_STATE, "this problem has no persistent coarse cycle");
+  const CyclePlan& pl = it->second;
+  if (pl.nphases < 2) fail(AMGSYM_ERR_STATE, "the coarse cycle has no grid barrier");
+  CycleBar b = D->bar;
+  b.extra = 1;      // one arrival more than the grid: nothing releases the first barrier
+  b.spins = 4096;   // a few milliseconds
+  const cudaError_t e = launch_cycle(mt, vt, c.C, pl.grid, pl.phases, pl.nphases, b, nullptr, c.st);
+  if (e != cudaSuccess) fail(AMGSYM_ERR_CUDA, std::string("coarse-cycle launch: ") + cudaGetErrorString(e));
+  CK(cudaStreamSynchronize(c.st));
+  int32_t err = 0;
+  CK(cudaMemcpy(&err, D->bar.err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(D->bar.count, 0, 4 * sizeof(unsigned)));  // count, generation, error
+  if (err != 1) fail(AMGSYM_ERR_CUDA, "the timed-out barrier wait was not reported");
   API_END
 }
 

@@ -44,8 +44,20 @@ struct GraphKey {
   int mode = -1;
   int32_t nrhs = 0;
   double tol = 0.0;
-  bool operator==(const GraphKey& o) const { return mode == o.mode && nrhs == o.nrhs && tol == o.tol; }
+  uint64_t tiles_gen = 0;  // tiles the captured launches were built with
+  bool operator==(const GraphKey& o) const {
+    return mode == o.mode && nrhs == o.nrhs && tol == o.tol && tiles_gen == o.tiles_gen;
+  }
 };
+
+// Phases of the persistent coarse-cycle kernel for one column count,
+// precision and set of work arrays (device array in the work allocations).
+struct CyclePlan {
+  CyclePhase* phases = nullptr;
+  int32_t nphases = 0;
+  int grid = 0;
+};
+using CycleKey = std::tuple<int32_t, int, int, uint64_t, uint64_t>;  // C, vt, mt, work_gen, tiles_gen
 
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
@@ -61,7 +73,8 @@ using TileKey = std::tuple<const void*, int32_t, int, int, int>;  // matrix idx 
 
 struct Device {
   int device_id = 0;
-  uint64_t work_gen = 0;  // bumped whenever work arrays are (re)allocated
+  uint64_t work_gen = 0;   // bumped whenever work arrays are (re)allocated
+  uint64_t tiles_gen = 0;  // bumped whenever the tuner changes tiles
   std::map<TileKey, Tile> tiles;
   std::set<std::tuple<int32_t, int, int>> tuned;  // (C, vt, mt) already tuned
   int precisions = 3;
@@ -86,6 +99,12 @@ struct Device {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   GraphCache graph;
   int64_t graph_kernels = 0;
+  // persistent coarse cycle: first level it runs (-1 = none), barrier words,
+  // whether a cooperative launch can be captured in a graph (-1 = not probed)
+  int fuse_level = -1;
+  CycleBar bar;
+  int coop_ok = -1;
+  std::map<CycleKey, CyclePlan> cycle_plans;
 };
 
 struct Ctx {
@@ -97,7 +116,13 @@ struct Ctx {
   cudaStream_t st;
   const int32_t* skip = nullptr;  // early-exit flag (active RHS count) of the PCG loop
   bool tune = false;              // run the tile autotuner before the first PCG loop
+  bool fuse = false;              // coarse levels as one persistent kernel (Device::fuse_level)
 };
+
+// Build (outside graph capture) the persistent coarse-cycle plan the V-cycle
+// of this context will use, and check the barrier error word after a run.
+void prepare_cycle(const Ctx& c);
+void check_cycle_error(Device* D, cudaStream_t st);
 
 
 void ensure_work(Device* D, int32_t nrhs, VecType vt);

@@ -50,9 +50,33 @@ template <typename T, int N>
 __device__ __forceinline__ Vec<T, N> ldv(const T* p) {
   return *reinterpret_cast<const Vec<T, N>*>(p);
 }
+// The same load through L2 only (ld.global.cg): coherent with what other
+// blocks of the same launch wrote before a grid barrier (the persistent
+// coarse-cycle kernel), unlike the read-only data path.
 template <typename T, int N>
-__device__ __forceinline__ Vec<T, N> ldv_stream(const T* p) {
-  return __ldcs(reinterpret_cast<const Vec<T, N>*>(p));
+__device__ __forceinline__ Vec<T, N> ldv_cg(const T* p) {
+  Vec<T, N> r;
+  constexpr int B = (int)sizeof(T) * N;
+  if constexpr (B % 16 == 0) {
+#pragma unroll
+    for (int i = 0; i < B / 16; ++i) reinterpret_cast<uint4*>(&r)[i] = __ldcg(reinterpret_cast<const uint4*>(p) + i);
+  } else if constexpr (B % 8 == 0) {
+#pragma unroll
+    for (int i = 0; i < B / 8; ++i) reinterpret_cast<uint2*>(&r)[i] = __ldcg(reinterpret_cast<const uint2*>(p) + i);
+  } else {
+    static_assert(B % 4 == 0, "vector of 4-byte multiples");
+#pragma unroll
+    for (int i = 0; i < B / 4; ++i)
+      reinterpret_cast<unsigned*>(&r)[i] = __ldcg(reinterpret_cast<const unsigned*>(p) + i);
+  }
+  return r;
+}
+template <typename T, int N, bool COH>
+__device__ __forceinline__ Vec<T, N> ldx(const T* p) {
+  if constexpr (COH)
+    return ldv_cg<T, N>(p);
+  else
+    return ldv<T, N>(p);
 }
 template <typename T, int N>
 __device__ __forceinline__ void stv(T* p, const Vec<T, N>& v) {
@@ -84,7 +108,7 @@ struct ComputeOf<double, double> {
 // runs over the diagonals in ascending offset, i.e. column, order -- the
 // order of the CSR loop -- and skips columns outside [0, rows); padded
 // positions inside hold 0 and add fma(0, x, acc) = acc.
-template <typename MT, typename XT, typename CT, int CPT>
+template <typename MT, typename XT, typename CT, int CPT, bool COH>
 __device__ __forceinline__ void dia_row(const SpmmArgs& a, int row, int c0, CT (&acc)[CPT]) {
   const MT* __restrict__ dv = static_cast<const MT*>(a.dval);
   const XT* __restrict__ X = static_cast<const XT*>(a.X);
@@ -102,7 +126,7 @@ __device__ __forceinline__ void dia_row(const SpmmArgs& a, int row, int c0, CT (
         const bool ok = d < a.ndiag && (unsigned)j < (unsigned)a.rows;
         m[u] = ok ? cvt<CT>(dv[(int64_t)a.dsrc[d] * n + row + a.dshift[d]]) : (CT)0;
         if (ok) {
-          x[u] = ldv<XT, CPT>(X + (int64_t)j * a.C + c0);
+          x[u] = ldx<XT, CPT, COH>(X + (int64_t)j * a.C + c0);
         } else {
 #pragma unroll
           for (int q = 0; q < CPT; ++q) x[u].v[q] = (XT)0;
@@ -126,8 +150,10 @@ __device__ __forceinline__ void dia_row(const SpmmArgs& a, int row, int c0, CT (
 // when KL > 1), and entry lane 0 runs the epilogue.  KL > 1 keeps several
 // gathers of one row in flight (the ptr -> idx -> X latency chain) and spreads
 // the long rows of the coarse levels over many lanes.  DIA: the matrix is in
-// the diagonal-offset form (one lane per row, no row pointers).
-template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE, bool DIA = false>
+// the diagonal-offset form (one lane per row, no row pointers).  COH: vector
+// operands are loaded through L2 only (written earlier in the same launch).
+template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE, bool DIA = false,
+          bool COH = false>
 __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int slot_step, int row_end,
                                           typename AccOf<XT>::type (&dpart)[CPT]) {
   static_assert(!DIA || KL == 1, "the diagonal-offset form runs one entry lane per row");
@@ -189,8 +215,8 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
       // interface flag word and epilogue operand loaded with the row pointers,
       // off the critical path of the gathers
       const uint32_t iface_word = (HAS_IFACE && e == 0) ? __ldg(a.imask + (row >> 5)) : 0u;
-      if (ZPF && e == 0 && a.beta != 0.0) zpre = ldv<XT, CPT>(Z + (int64_t)row * C + c0);
-      if (DIA) dia_row<MT, XT, CT, CPT>(a, row, c0, acc);
+      if (ZPF && e == 0 && a.beta != 0.0) zpre = ldx<XT, CPT, COH>(Z + (int64_t)row * C + c0);
+      if (DIA) dia_row<MT, XT, CT, CPT, COH>(a, row, c0, acc);
       int k = DIA ? ke : kb + e;  // the diagonal form has no CSR entries
       // U entries per step, predicated: all index/value loads first, then all
       // gathers, so a row of up to U * KL entries costs one round trip and a
@@ -209,7 +235,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (k + u * KL < ke) {
-            x[u] = ldv<XT, CPT>(X + (int64_t)j[u] * C + c0);
+            x[u] = ldx<XT, CPT, COH>(X + (int64_t)j[u] * C + c0);
           } else {
 #pragma unroll
             for (int q = 0; q < CPT; ++q) x[u].v[q] = (XT)0;
@@ -229,7 +255,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
           const CT* __restrict__ iv = static_cast<const CT*>(a.ival);
           for (int ee = __ldg(a.iptr + f); ee < __ldg(a.iptr + f + 1); ++ee) {
             const int j = __ldg(a.icol + ee);
-            const Vec<XT, CPT> xv = ldv<XT, CPT>(X + (int64_t)j * C + c0);
+            const Vec<XT, CPT> xv = ldx<XT, CPT, COH>(X + (int64_t)j * C + c0);
 #pragma unroll
             for (int q = 0; q < CPT; ++q) {
               const int blk = (c0 + q) % a.nb;
@@ -249,7 +275,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
     if (live && e == 0) {
       Vec<OT, CPT> out;
       if (a.beta != 0.0) {
-        const Vec<XT, CPT> zv = ZPF ? zpre : ldv<XT, CPT>(Z + (int64_t)row * C + c0);
+        const Vec<XT, CPT> zv = ZPF ? zpre : ldx<XT, CPT, COH>(Z + (int64_t)row * C + c0);
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
           const CT y = alpha * acc[q] + beta * (CT)zv.v[q];
@@ -267,7 +293,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
       stv<OT, CPT>(Y + (int64_t)row * C + c0, out);
       if (HAS_DOT) {
         if (a.dot.mode == DOT_WY) {
-          const Vec<XT, CPT> wv = ldv<XT, CPT>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
+          const Vec<XT, CPT> wv = ldx<XT, CPT, COH>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
 #pragma unroll
           for (int q = 0; q < CPT; ++q) dpart[q] += (DT)wv.v[q] * (DT)acc[q];
         } else {
