@@ -214,17 +214,23 @@ class ClockSampler:
 
 def _spmm_roofline(P, amg, torch, nrhs: int, reps: int = 30):
     """Time the reduced SpMM (FP32 values and vectors, interface fused) alone:
-    per-launch CUDA events on the launching stream, L2 flushed between launches."""
+    per-launch CUDA events on the launching stream, L2 flushed between launches:
+    a 256 MiB buffer is written (evicting every line) and then a second one is
+    read, so the write-backs of the dirty flush lines happen before the timed
+    launch instead of inside it."""
     sz = P.sizes()
     C = nrhs * P.nb
     n_b = P.n_b
     X = torch.randn((n_b, C), dtype=torch.float32, device="cuda")
     Y = torch.empty_like(X)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clean = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sink = torch.empty((), dtype=torch.float32, device="cuda")
     st = torch.cuda.current_stream()
     ts = []
     for i in range(reps + 3):
         flush.zero_()
+        torch.sum(clean, dim=0, out=sink)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)

@@ -79,7 +79,7 @@ enum {
 typedef struct {
   double strength_theta;    /* classical strength threshold, default 0.25 */
   double interp_trunc;      /* drop interpolation weights < trunc * row max, 0.2 */
-  int32_t interp_max_elems; /* keep at most this many weights per row, 4 */
+  int32_t interp_max_elems; /* keep at most this many weights per row, 3 */
   int32_t max_levels;       /* hierarchy depth limit, 25 */
   int32_t coarse_max;       /* dense direct solve at or below this size, 256 */
   int32_t fsai_max_lower;   /* FSAI pattern: strongest lower entries per row,

@@ -49,7 +49,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   if (!o) return;
   o->strength_theta = 0.25;
   o->interp_trunc = 0.2;
-  o->interp_max_elems = 4;
+  o->interp_max_elems = 3;
   o->max_levels = 25;
   o->coarse_max = 256;
   o->fsai_max_lower = 4;
