@@ -30,8 +30,10 @@ struct DevCsr {
   const void* vals(ValType t) const {
     return t == VAL_F64 ? (const void*)v64 : t == VAL_F32 ? (const void*)v32 : (const void*)v16;
   }
-  // Diagonal-offset copy (ndiag > 0; layout and indexing as the host Dia):
-  // [nstored][rows] values per precision built.
+  // Diagonal-offset copy (ndiag > 0; indexing as the host Dia): [nstored]
+  // value arrays of dstride >= rows elements (rows rounded up to 8, zero
+  // padded, so every array starts 16-byte aligned) per precision built.
+  int64_t dstride = 0;
   int32_t ndiag = 0;
   int32_t doff[kMaxDiag] = {}, dsrc[kMaxDiag] = {}, dshift[kMaxDiag] = {};
   double* dv64 = nullptr;
@@ -131,9 +133,10 @@ struct SpmmArgs {
   int32_t cpt = 0;
   // Diagonal-offset form (ndiag > 0 selects it; ptr/idx/val unused): the
   // entry (row, row + doff[d]) exists when that column is in [0, rows) and
-  // has the value dval[dsrc[d] * rows + row + dshift[d]].
+  // has the value dval[dsrc[d] * dstride + row + dshift[d]].
   int32_t ndiag = 0;
   int32_t doff[kMaxDiag] = {}, dsrc[kMaxDiag] = {}, dshift[kMaxDiag] = {};
+  int64_t dstride = 0;
   const void* dval = nullptr;
   DotArgs dot;
 };

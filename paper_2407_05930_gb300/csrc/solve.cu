@@ -73,15 +73,22 @@ static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions
       D.dsrc[d] = dia->src[d];
       D.dshift[d] = dia->shift[d];
     }
-    const int64_t cnt = (int64_t)dia->val.size();
-    if (precisions & 1) D.dv64 = upload(owner, dia->val.data(), cnt);
+    // arrays of dstride elements: rows rounded up to 8, zero padded
+    const int64_t rows = M.rows;
+    D.dstride = (rows + 7) / 8 * 8;
+    const int64_t cnt = D.dstride * dia->nstored;
+    std::vector<double> padded((size_t)cnt, 0.0);
+    for (int q = 0; q < dia->nstored; ++q)
+      std::copy(dia->val.begin() + (size_t)q * rows, dia->val.begin() + (size_t)(q + 1) * rows,
+                padded.begin() + (size_t)q * D.dstride);
+    if (precisions & 1) D.dv64 = upload(owner, padded.data(), cnt);
     if (precisions & 2) {
-      std::vector<float> v(dia->val.begin(), dia->val.end());
+      std::vector<float> v(padded.begin(), padded.end());
       D.dv32 = upload(owner, v.data(), cnt);
     }
     if (precisions & 4) {
       std::vector<__nv_bfloat16> v(cnt);
-      for (int64_t i = 0; i < cnt; ++i) v[i] = __float2bfloat16((float)dia->val[i]);
+      for (int64_t i = 0; i < cnt; ++i) v[i] = __float2bfloat16((float)padded[i]);
       D.dv16 = upload(owner, v.data(), cnt);
     }
   }
@@ -330,6 +337,7 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
       a.dshift[d] = M.dshift[d];
     }
     a.dval = M.dvals(mt);
+    a.dstride = M.dstride;
   }
   if (dot) a.dot = *dot;
   a.skip = c.skip;
