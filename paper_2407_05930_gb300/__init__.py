@@ -63,6 +63,7 @@ class Opts(ctypes.Structure):
         ("coarse_drop", ctypes.c_double),
         ("dia_max_diag", ctypes.c_int32),
         ("fuse_rows", ctypes.c_int32),
+        ("fsai_max_lower_coarse", ctypes.c_int32),
     ]
 
 

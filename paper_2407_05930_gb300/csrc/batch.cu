@@ -399,13 +399,43 @@ static void plan_vcycle(Batch* B, std::vector<BLaunch>& plan, std::vector<Ctx>& 
   };
   auto L_ = [&](int p) -> const DevLevel& { return ctx[p].D->lv[l]; };
   const int nu = ctx[deep[0]].D->nu;
+  // Smoother steps as smooth_first / smooth_sweep of the single-problem
+  // V-cycle: a problem whose G_l is diagonal takes one elementwise step, the
+  // others the two FSAI products (the one carrying a fused dot always does).
+  auto smooth = [&](bool first, bool fin) {
+    std::vector<UpdArgs> jac;
+    std::vector<SpmmArgs> g, gt;
+    for (size_t k = 0; k < deep.size(); ++k) {
+      const int p = deep[k];
+      const void* jd = L_(p).jd(vt);
+      if (jd && !fin) {
+        UpdArgs a;
+        a.rows = L_(p).n;
+        a.C = ctx[p].C;
+        a.x = dz[k];
+        a.p = first ? dy[k] : lw(p).r;
+        a.jd = jd;
+        a.accumulate = first ? 0 : 1;
+        a.skip = ctx[p].skip;
+        jac.push_back(a);
+      } else {
+        g.push_back(make_spmm_args(ctx[p], L_(p).G, mt, vt, vt, first ? dy[k] : lw(p).r, lw(p).t, 1.0, 0.0, nullptr,
+                                   false, nullptr));
+        gt.push_back(make_spmm_args(ctx[p], L_(p).Gt, mt, vt, vt, lw(p).t, dz[k], L_(p).omega, first ? 0.0 : 1.0,
+                                    first ? nullptr : dz[k], false, fin ? &dlast[k] : nullptr));
+      }
+    }
+    add_vec(B, plan, BOP_JACOBI, vt, jac);
+    if (!g.empty()) {
+      add_spmm(B, plan, g, mt, vt, vt);
+      add_spmm(B, plan, gt, mt, vt, vt);
+    }
+  };
   // presmoothing from zero, extra sweeps, residual, restriction
-  phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).G, mt, vt, vt, dy[k], lw(p).t, 1.0, 0.0, nullptr, false, nullptr); });
-  phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).Gt, mt, vt, vt, lw(p).t, dz[k], L_(p).omega, 0.0, nullptr, false, nullptr); });
+  smooth(true, false);
   for (int s = 1; s < nu; ++s) {
     phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).A, mt, vt, vt, dz[k], lw(p).r, -1.0, 1.0, dy[k], ctx[p].finest_hat && l == 0, nullptr); });
-    phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).G, mt, vt, vt, lw(p).r, lw(p).t, 1.0, 0.0, nullptr, false, nullptr); });
-    phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).Gt, mt, vt, vt, lw(p).t, dz[k], L_(p).omega, 1.0, dz[k], false, nullptr); });
+    smooth(false, false);
   }
   phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).A, mt, vt, vt, dz[k], lw(p).r, -1.0, 1.0, dy[k], ctx[p].finest_hat && l == 0, nullptr); });
   phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).R, mt, vt, vt, lw(p).r, cw(p).y, 1.0, 0.0, nullptr, false, nullptr); });
@@ -422,11 +452,7 @@ static void plan_vcycle(Batch* B, std::vector<BLaunch>& plan, std::vector<Ctx>& 
   for (int s = 0; s < nu; ++s) {
     const bool fin = (s == nu - 1) && last;
     phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).A, mt, vt, vt, dz[k], lw(p).r, -1.0, 1.0, dy[k], ctx[p].finest_hat && l == 0, nullptr); });
-    phase([&](size_t k, int p) { return make_spmm_args(ctx[p], L_(p).G, mt, vt, vt, lw(p).r, lw(p).t, 1.0, 0.0, nullptr, false, nullptr); });
-    phase([&](size_t k, int p) {
-      return make_spmm_args(ctx[p], L_(p).Gt, mt, vt, vt, lw(p).t, dz[k], L_(p).omega, 1.0, dz[k], false,
-                            fin ? &dlast[k] : nullptr);
-    });
+    smooth(false, fin);
   }
 }
 

@@ -63,6 +63,11 @@ struct DevLevel {
   DevCsr A, P, R, G, Gt;
   double omega = 1.0;
   double* cinv = nullptr;  // coarsest: dense inverse, FP64 row-major n x n
+  // Diagonal G (an FSAI pattern of one entry per row): the smoother omega G^T G
+  // is the diagonal jd = omega g_ii^2, applied elementwise (damped Jacobi).
+  double* jd64 = nullptr;
+  float* jd32 = nullptr;
+  const void* jd(VecType t) const { return t == VEC_F64 ? (const void*)jd64 : (const void*)jd32; }
 };
 
 // Per-column CG scalars and solve status (device).
@@ -165,6 +170,10 @@ void launch_zero(VecType vt, int64_t count, void* dst, cudaStream_t st);
 void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,
                 cudaStream_t st, const int32_t* skip = nullptr);
 // Z = Ainv Y (dense coarsest solve, FP64 arithmetic)
+// Diagonal smoother step: z = jd o src (accumulate = 0) or z += jd o src
+// (accumulate = 1), jd one value per row, src and z [rows][C].
+void launch_jacobi(VecType vt, int64_t rows, int32_t C, const void* jd, const void* src, void* z, int accumulate,
+                   cudaStream_t st, const int32_t* skip = nullptr);
 void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
                          cudaStream_t st, const int32_t* skip = nullptr);
 // *dst = v (a one-thread kernel, so the write is ordered on the stream and capturable)
@@ -220,12 +229,14 @@ struct BDot {
 // Arguments of one problem for the batched vector kernels.
 struct UpdArgs {
   int32_t rows = 0, C = 0;
-  void* x = nullptr;        // update1: x ; update2: p ; copy: dst ; add: y (f64)
+  void* x = nullptr;        // update1: x ; update2: p ; copy: dst ; add: y (f64) ; jacobi: z
   void* r = nullptr;        // update1: r
-  const void* p = nullptr;  // update1: p ; update2: z ; copy/add: src
+  const void* p = nullptr;  // update1: p ; update2: z ; copy/add: src ; jacobi: src
   const void* q = nullptr;  // update1: q
   const double* beta = nullptr;
   const int32_t* skip = nullptr;
+  const void* jd = nullptr;  // jacobi: one value per row
+  int32_t accumulate = 0;    // jacobi: z += jd o src instead of z = jd o src
   DotArgs dot;
 };
 
@@ -238,16 +249,25 @@ struct CoarseArgs {
   const int32_t* skip = nullptr;
 };
 
-enum BatchVecOp { BOP_UPDATE1 = 0, BOP_UPDATE2 = 1, BOP_COPY = 2 };
+enum BatchVecOp { BOP_UPDATE1 = 0, BOP_UPDATE2 = 1, BOP_COPY = 2, BOP_JACOBI = 3 };
 
 // ---------------------------------------------------------------------------
 // Persistent coarse-cycle kernel (k_cycle.cu): the phases of the V-cycle over
 // the coarsest levels, one cooperative launch, grid barriers between phases.
-enum CycleKind { CYCLE_SPMM = 0, CYCLE_DENSE = 1 };
+enum CycleKind { CYCLE_SPMM = 0, CYCLE_DENSE = 1, CYCLE_JACOBI = 2 };
+// Diagonal smoother step (as launch_jacobi).
+struct JacobiArgs {
+  int64_t rows = 0;
+  int32_t C = 0, accumulate = 0;
+  const void* jd = nullptr;
+  const void* src = nullptr;
+  void* z = nullptr;
+};
 struct CyclePhase {
   int32_t kind = CYCLE_SPMM;
   SpmmArgs a;    // CYCLE_SPMM (no dot, no interface; a.kl = entry lanes)
   CoarseArgs c;  // CYCLE_DENSE
+  JacobiArgs j;  // CYCLE_JACOBI
 };
 // Grid barrier words (device): arrivals, generation, error flag (1 = a wait
 // ran out; the launch stopped early).

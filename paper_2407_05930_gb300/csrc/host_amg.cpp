@@ -583,7 +583,7 @@ void build_hierarchy(const Csr& A0, const amgsym_opts& o, HostHierarchy& H) {
       L.coarse_inv = dense_inverse(L.A);
       break;
     }
-    L.G = fsai(L.A, o.fsai_max_lower);
+    L.G = fsai(L.A, lev == 0 ? o.fsai_max_lower : o.fsai_max_lower_coarse);
     L.Gt = transpose(L.G);
     L.lambda_max = lambda_max_GAGt(L.A, L.G, L.Gt, o.seed + 17 * (uint64_t)lev);
     L.omega = (L.lambda_max > 0.0) ? o.omega_scale / L.lambda_max : 1.0;
@@ -691,7 +691,8 @@ extern "C" amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts) {
   if (opts) o = *opts;
   if (o.nu < 1 || o.nu > 8) fail(AMGSYM_ERR_ARG, "nu must be in [1, 8]");
   if (o.fuse_rows < 0 || o.dia_max_diag < 0) fail(AMGSYM_ERR_ARG, "fuse_rows and dia_max_diag must be >= 0");
-  if (o.fsai_max_lower < 1 || o.fsai_max_lower > 32) fail(AMGSYM_ERR_ARG, "fsai_max_lower must be in [1, 32]");
+  if (o.fsai_max_lower < 1 || o.fsai_max_lower > 32 || o.fsai_max_lower_coarse < 1 || o.fsai_max_lower_coarse > 32)
+    fail(AMGSYM_ERR_ARG, "fsai_max_lower and fsai_max_lower_coarse must be in [1, 32]");
   if (o.coarse_max < 1 || o.coarse_max > kDenseLimit) fail(AMGSYM_ERR_ARG, "coarse_max out of range");
   if (o.max_levels < 1) fail(AMGSYM_ERR_ARG, "max_levels must be >= 1");
   if ((o.precisions & 7) == 0) fail(AMGSYM_ERR_ARG, "precisions mask is empty");

@@ -61,6 +61,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->coarse_drop = 0.003;
   o->dia_max_diag = AMGSYM_MAX_DIAG;
   o->fuse_rows = 0;
+  o->fsai_max_lower_coarse = 1;
 }
 
 extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {

@@ -183,6 +183,26 @@ __global__ void __launch_bounds__(kBlock) vec_batch_kernel(const UpdArgs* __rest
           for (int k = 0; k < CPT; ++k) pv.v[k] = zv.v[k] + b[k] * pv.v[k];
           *reinterpret_cast<V*>(p + o) = pv;
         }
+      } else if (OP == BOP_JACOBI) {
+        // the diagonal smoother step of the stand-alone jacobi kernel
+        T* z = static_cast<T*>(a.x);
+        const T* src = static_cast<const T*>(a.p);
+        const T* jd = static_cast<const T*>(a.jd);
+        for (int64_t row = (int64_t)bi.first_slot * rows_pb + rloc; row < bi.row_end; row += rows_pb) {
+          const int64_t o = row * C + c0;
+          const T d = jd[row];
+          const V sv = *reinterpret_cast<const V*>(src + o);
+          V zv;
+          if (a.accumulate) {
+            zv = *reinterpret_cast<const V*>(z + o);
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) zv.v[k] = fma(d, sv.v[k], zv.v[k]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) zv.v[k] = d * sv.v[k];
+          }
+          *reinterpret_cast<V*>(z + o) = zv;
+        }
       } else {
         T* d = static_cast<T*>(a.x);
         const T* s = static_cast<const T*>(a.p);
@@ -213,6 +233,8 @@ static void vec_batch_c(int op, const UpdArgs* args, const BItem* items, int32_t
     run(vec_batch_kernel<T, CPT, BOP_UPDATE1>);
   else if (op == BOP_UPDATE2)
     run(vec_batch_kernel<T, CPT, BOP_UPDATE2>);
+  else if (op == BOP_JACOBI)
+    run(vec_batch_kernel<T, CPT, BOP_JACOBI>);
   else
     run(vec_batch_kernel<T, CPT, BOP_COPY>);
 }

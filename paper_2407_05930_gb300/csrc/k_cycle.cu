@@ -81,6 +81,20 @@ __device__ __forceinline__ void dense_phase(const CoarseArgs& c) {
   }
 }
 
+// Diagonal smoother step, the arithmetic of the stand-alone jacobi kernel.
+template <typename XT>
+__device__ __forceinline__ void jacobi_phase(const JacobiArgs& j) {
+  const int64_t total = j.rows * j.C;
+  const XT* __restrict__ jd = static_cast<const XT*>(j.jd);
+  const XT* src = static_cast<const XT*>(j.src);  // written earlier in the launch: L2 loads
+  XT* z = static_cast<XT*>(j.z);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const XT d = __ldg(jd + e / j.C);
+    const XT sv = ldv_cg<XT, 1>(src + e).v[0];
+    z[e] = j.accumulate ? fma(d, sv, ldv_cg<XT, 1>(z + e).v[0]) : d * sv;
+  }
+}
+
 template <typename MT, typename XT, int CPT>
 __global__ void __launch_bounds__(kBlock, 2)
     cycle_kernel(const CyclePhase* __restrict__ phases, int32_t nphases, CycleBar bar, const int32_t* skip) {
@@ -98,6 +112,8 @@ __global__ void __launch_bounds__(kBlock, 2)
     __syncthreads();
     if (ph.kind == CYCLE_DENSE) {
       dense_phase<XT>(ph.c);
+    } else if (ph.kind == CYCLE_JACOBI) {
+      jacobi_phase<XT>(ph.j);
     } else {
       DT dpart[CPT];
       const SpmmArgs& a = ph.a;

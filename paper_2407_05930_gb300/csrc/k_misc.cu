@@ -316,6 +316,48 @@ void launch_cg_update2(VecType vt, int64_t rows, int32_t C, void* p, const void*
     update2_t<float>(rows, C, p, z, beta, st, skip);
 }
 
+// Diagonal smoother step (a diagonal FSAI factor: omega G^T G = diag(jd)).
+// One thread per row slice of V columns: z = jd[row] * src (or + z, fused).
+template <typename T, int V>
+__global__ void __launch_bounds__(kBlock) jacobi_kernel(int64_t rows, int32_t C, const T* __restrict__ jd,
+                                                        const T* __restrict__ src, T* z, int accumulate,
+                                                        const int32_t* skip) {
+  if (skip && *skip == 0) return;
+  const int64_t slices = (int64_t)rows * (C / V);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < slices; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = t / (C / V);
+    const T d = jd[row];
+    const int64_t e = t * V;
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const T s = src[e + q];
+      z[e + q] = accumulate ? fma(d, s, z[e + q]) : d * s;
+    }
+  }
+}
+
+void launch_jacobi(VecType vt, int64_t rows, int32_t C, const void* jd, const void* src, void* z, int accumulate,
+                   cudaStream_t st, const int32_t* skip) {
+  count_launch();
+  if (vt == VEC_F64) {
+    const double* j = static_cast<const double*>(jd);
+    const double* s = static_cast<const double*>(src);
+    double* d = static_cast<double*>(z);
+    if (C % 2 == 0)
+      jacobi_kernel<double, 2><<<grid_for(rows * (C / 2), kBlock), kBlock, 0, st>>>(rows, C, j, s, d, accumulate, skip);
+    else
+      jacobi_kernel<double, 1><<<grid_for(rows * C, kBlock), kBlock, 0, st>>>(rows, C, j, s, d, accumulate, skip);
+  } else {
+    const float* j = static_cast<const float*>(jd);
+    const float* s = static_cast<const float*>(src);
+    float* d = static_cast<float*>(z);
+    if (C % 4 == 0)
+      jacobi_kernel<float, 4><<<grid_for(rows * (C / 4), kBlock), kBlock, 0, st>>>(rows, C, j, s, d, accumulate, skip);
+    else
+      jacobi_kernel<float, 1><<<grid_for(rows * C, kBlock), kBlock, 0, st>>>(rows, C, j, s, d, accumulate, skip);
+  }
+}
+
 template <typename T>
 __global__ void add_to_f64_kernel(int64_t count, double* __restrict__ y, const T* __restrict__ x) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)

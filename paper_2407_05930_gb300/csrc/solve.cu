@@ -152,6 +152,18 @@ void device_upload(amgsym_problem* p) {
       V.R = upload_csr(D->owned, L.R, p->opts.precisions);
       V.G = upload_csr(D->owned, L.G, p->opts.precisions, &L.Gdia);
       V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions, &L.Gtdia);
+      // a diagonal FSAI factor: the smoother is the diagonal omega g_ii^2
+      bool diag = L.G.nnz() == L.G.rows;
+      for (int64_t i = 0; diag && i < L.G.rows; ++i) diag = L.G.idx[L.G.ptr[i]] == (int32_t)i;
+      if (diag && L.G.rows > 0) {
+        std::vector<double> jd((size_t)L.G.rows);
+        for (int64_t i = 0; i < L.G.rows; ++i) jd[i] = L.omega * L.G.val[L.G.ptr[i]] * L.G.val[L.G.ptr[i]];
+        if (p->opts.precisions & 1) V.jd64 = upload(D->owned, jd.data(), (int64_t)jd.size());
+        if (p->opts.precisions & 6) {
+          std::vector<float> j32(jd.begin(), jd.end());
+          V.jd32 = upload(D->owned, j32.data(), (int64_t)j32.size());
+        }
+      }
     }
   }
   D->Ainn = D->lv[0].A;
@@ -441,6 +453,36 @@ void tune_tiles(const Ctx& c) {
 }
 
 // ---------------------------------------------------------------------------
+// Smoother steps of the V-cycle (presmoothing from zero, then sweeps), with
+// the FSAI factor G_l of the level: z = w G^T G y and z += w G^T G (y - A z).
+// A diagonal G (one entry per row) is applied as the diagonal jd = w g_ii^2
+// in one elementwise kernel instead of two products.  `dot` (the fused
+// <r, z> of the final level-0 product) keeps the product form.
+
+static void smooth_first(const Ctx& c, const DevLevel& L, LevelWork& lw, const void* y, void* z) {
+  if (const void* jd = L.jd(c.vt)) {
+    launch_jacobi(c.vt, L.n, c.C, jd, y, z, 0, c.st, c.skip);
+    check_launch();
+    return;
+  }
+  spmm(c, L.G, c.mt, c.vt, c.vt, y, lw.t, 1.0, 0.0, nullptr, false, nullptr);
+  spmm(c, L.Gt, c.mt, c.vt, c.vt, lw.t, z, L.omega, 0.0, nullptr, false, nullptr);
+}
+
+static void smooth_sweep(const Ctx& c, const DevLevel& L, LevelWork& lw, const void* y, void* z, bool hat,
+                         const DotArgs* dot) {
+  spmm(c, L.A, c.mt, c.vt, c.vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+  const void* jd = L.jd(c.vt);
+  if (jd && !dot) {
+    launch_jacobi(c.vt, L.n, c.C, jd, lw.r, z, 1, c.st, c.skip);
+    check_launch();
+    return;
+  }
+  spmm(c, L.G, c.mt, c.vt, c.vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
+  spmm(c, L.Gt, c.mt, c.vt, c.vt, lw.t, z, L.omega, 1.0, z, false, dot);
+}
+
+// ---------------------------------------------------------------------------
 // Persistent coarse cycle (k_cycle.cu).  The phases are the products of
 // vcycle() below from level Device::fuse_level down, in the same order with
 // the same arguments, entry lanes and therefore the same sums.
@@ -478,23 +520,41 @@ static void cycle_phases(const Ctx& c, int l, const void* y, void* z, int kcpt, 
     out.push_back(ph);
     return;
   }
-  cycle_phase(c, out, L.G, y, lw.t, 1.0, 0.0, nullptr, kcpt);
-  cycle_phase(c, out, L.Gt, lw.t, z, L.omega, 0.0, nullptr, kcpt);
-  for (int k = 1; k < D->nu; ++k) {
+  // the smoother steps of smooth_first / smooth_sweep
+  const void* jd = L.jd(c.vt);
+  auto jacobi = [&](const void* src, int accumulate) {
+    CyclePhase ph;
+    ph.kind = CYCLE_JACOBI;
+    ph.j.rows = L.n;
+    ph.j.C = c.C;
+    ph.j.accumulate = accumulate;
+    ph.j.jd = jd;
+    ph.j.src = src;
+    ph.j.z = z;
+    out.push_back(ph);
+  };
+  auto sweep = [&]() {
     cycle_phase(c, out, L.A, z, lw.r, -1.0, 1.0, y, kcpt);
-    cycle_phase(c, out, L.G, lw.r, lw.t, 1.0, 0.0, nullptr, kcpt);
-    cycle_phase(c, out, L.Gt, lw.t, z, L.omega, 1.0, z, kcpt);
+    if (jd) {
+      jacobi(lw.r, 1);
+    } else {
+      cycle_phase(c, out, L.G, lw.r, lw.t, 1.0, 0.0, nullptr, kcpt);
+      cycle_phase(c, out, L.Gt, lw.t, z, L.omega, 1.0, z, kcpt);
+    }
+  };
+  if (jd) {
+    jacobi(y, 0);
+  } else {
+    cycle_phase(c, out, L.G, y, lw.t, 1.0, 0.0, nullptr, kcpt);
+    cycle_phase(c, out, L.Gt, lw.t, z, L.omega, 0.0, nullptr, kcpt);
   }
+  for (int k = 1; k < D->nu; ++k) sweep();
   cycle_phase(c, out, L.A, z, lw.r, -1.0, 1.0, y, kcpt);
   LevelWork& cw = W.lw[l + 1];
   cycle_phase(c, out, L.R, lw.r, cw.y, 1.0, 0.0, nullptr, kcpt);
   cycle_phases(c, l + 1, cw.y, cw.z, kcpt, out);
   cycle_phase(c, out, L.P, cw.z, z, 1.0, 1.0, z, kcpt);
-  for (int k = 0; k < D->nu; ++k) {
-    cycle_phase(c, out, L.A, z, lw.r, -1.0, 1.0, y, kcpt);
-    cycle_phase(c, out, L.G, lw.r, lw.t, 1.0, 0.0, nullptr, kcpt);
-    cycle_phase(c, out, L.Gt, lw.t, z, L.omega, 1.0, z, kcpt);
-  }
+  for (int k = 0; k < D->nu; ++k) sweep();
 }
 
 static CycleKey cycle_key(const Ctx& c) {
@@ -589,13 +649,8 @@ static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* l
   const ValType mt = c.mt;
   const VecType vt = c.vt;
   // presmoothing: the first sweep from zero is z = w G^T G y
-  spmm(c, L.G, mt, vt, vt, y, lw.t, 1.0, 0.0, nullptr, false, nullptr);
-  spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 0.0, nullptr, false, nullptr);
-  for (int k = 1; k < D->nu; ++k) {
-    spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
-    spmm(c, L.G, mt, vt, vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
-    spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 1.0, z, false, nullptr);
-  }
+  smooth_first(c, L, lw, y, z);
+  for (int k = 1; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, nullptr);
   // residual and restriction r_c = P^T (y - A z)
   spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
   LevelWork& cw = W.lw[l + 1];
@@ -604,11 +659,7 @@ static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* l
   // prolongation and update z += P z_c
   spmm(c, L.P, mt, vt, vt, cw.z, z, 1.0, 1.0, z, false, nullptr);
   // postsmoothing
-  for (int k = 0; k < D->nu; ++k) {
-    spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
-    spmm(c, L.G, mt, vt, vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
-    spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 1.0, z, false, k == D->nu - 1 ? last : nullptr);
-  }
+  for (int k = 0; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, k == D->nu - 1 ? last : nullptr);
 }
 
 DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb,
@@ -1055,23 +1106,14 @@ void vcycle_with(const Ctx& c, std::vector<LevelWork>& lws, int l, const void* y
   const bool hat = c.finest_hat && l == 0;
   const ValType mt = c.mt;
   const VecType vt = c.vt;
-  spmm(c, L.G, mt, vt, vt, y, lw.t, 1.0, 0.0, nullptr, false, nullptr);
-  spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 0.0, nullptr, false, nullptr);
-  for (int k = 1; k < D->nu; ++k) {
-    spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
-    spmm(c, L.G, mt, vt, vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
-    spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 1.0, z, false, nullptr);
-  }
+  smooth_first(c, L, lw, y, z);
+  for (int k = 1; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, nullptr);
   spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
   LevelWork& cw = lws[l + 1];
   spmm(c, L.R, mt, vt, vt, lw.r, cw.y, 1.0, 0.0, nullptr, false, nullptr);
   vcycle_with(c, lws, l + 1, cw.y, cw.z);
   spmm(c, L.P, mt, vt, vt, cw.z, z, 1.0, 1.0, z, false, nullptr);
-  for (int k = 0; k < D->nu; ++k) {
-    spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
-    spmm(c, L.G, mt, vt, vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
-    spmm(c, L.Gt, mt, vt, vt, lw.t, z, L.omega, 1.0, z, false, nullptr);
-  }
+  for (int k = 0; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, nullptr);
 }
 
 }  // namespace
