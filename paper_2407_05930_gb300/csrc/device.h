@@ -53,6 +53,7 @@ struct DevIface {
   uint32_t* mask = nullptr;    // ceil(n_b / 32)
   int32_t* prefix = nullptr;   // ceil(n_b / 32)
   int32_t* iptr = nullptr;     // n_rows_flagged + 1
+  int32_t* irows = nullptr;    // n_rows_flagged: the flagged rows, ascending
   int32_t* icol = nullptr;     // n_entries
   double* ival64 = nullptr;    // n_entries * nb
   float* ival32 = nullptr;     // n_entries * nb
@@ -126,6 +127,8 @@ struct SpmmArgs {
   const uint32_t* imask = nullptr;
   const int32_t* iprefix = nullptr;
   const int32_t* iptr = nullptr;
+  const int32_t* irows = nullptr;  // flagged rows, ascending (the second pass)
+  int32_t nflag = 0;
   const int32_t* icol = nullptr;
   const void* ival = nullptr;  // same precision class as the accumulation
   int32_t nb = 1;

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kBlock, 4)
     DT dpart[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) dpart[q] = (DT)0;
-    spmm_tile<MT, XT, OT, CPT, KL, HAS_DOT, HAS_IFACE, DIA>(a, bi.first_slot, 1, bi.row_end, dpart);
+    spmm_tile<MT, XT, OT, CPT, KL, HAS_DOT, HAS_IFACE, DIA>(a, bi.first_slot, 1, bi.row_end, dpart, false);
     if (HAS_DOT) {
       const TileLayout t = tile_layout<CPT, KL>(a.C);
       double part[CPT];

@@ -172,12 +172,13 @@ void device_upload(amgsym_problem* p) {
   if (ne > 0) {
     const int64_t words = (p->n_b + 31) / 32;
     std::vector<uint32_t> mask(words, 0);
-    std::vector<int32_t> prefix(words, 0), iptr;
+    std::vector<int32_t> prefix(words, 0), iptr, irows;
     for (int64_t e = 0; e < ne; ++e) {
       const int32_t r = p->irow[e];
       if (e == 0 || p->irow[e - 1] != r) {
         mask[r >> 5] |= 1u << (r & 31);
         iptr.push_back((int32_t)e);
+        irows.push_back(r);
       }
     }
     iptr.push_back((int32_t)ne);
@@ -191,6 +192,7 @@ void device_upload(amgsym_problem* p) {
     D->iface.mask = upload(D->owned, mask.data(), words);
     D->iface.prefix = upload(D->owned, prefix.data(), words);
     D->iface.iptr = upload(D->owned, iptr.data(), (int64_t)iptr.size());
+    D->iface.irows = upload(D->owned, irows.data(), (int64_t)irows.size());
     D->iface.icol = upload(D->owned, p->icol.data(), ne);
     D->iface.ival64 = upload(D->owned, p->ivals.data(), ne * p->nb);
     std::vector<float> v32(p->ivals.begin(), p->ivals.end());
@@ -336,6 +338,8 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
     a.imask = c.D->iface.mask;
     a.iprefix = c.D->iface.prefix;
     a.iptr = c.D->iface.iptr;
+    a.irows = c.D->iface.irows;
+    a.nflag = c.D->iface.n_rows_flagged;
     a.icol = c.D->iface.icol;
     const bool f64 = (mt == VAL_F64) || (xt == VEC_F64);
     a.ival = f64 ? (const void*)c.D->iface.ival64 : (const void*)c.D->iface.ival32;

@@ -160,6 +160,106 @@ __device__ __forceinline__ void dia_row(const SpmmArgs& a, int row, int c0, CT (
   }
 }
 
+// The CSR entries kb + e, kb + e + KL, ... < ke of one row, U per step,
+// predicated: all index/value loads first, then all gathers, so a row of up
+// to U * KL entries costs one round trip and a 7-point row (U = 4) two, with
+// every gather of a step in flight at once.
+template <typename MT, typename XT, typename CT, int CPT, int KL, bool COH>
+__device__ __forceinline__ void csr_row(const SpmmArgs& a, int kb, int ke, int e, int c0, CT (&acc)[CPT]) {
+  const MT* __restrict__ val = static_cast<const MT*>(a.val);
+  const XT* __restrict__ X = static_cast<const XT*>(a.X);
+  const int32_t* __restrict__ idx = a.idx;
+  const int C = a.C;
+  constexpr int U = CPT >= 8 ? 2 : 4;
+  for (int k = kb + e; k < ke; k += U * KL) {
+    int j[U];
+    CT m[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = k + u * KL < ke;
+      j[u] = ok ? __ldg(idx + k + u * KL) : 0;
+      m[u] = ok ? cvt<CT>(val[k + u * KL]) : (CT)0;
+    }
+    Vec<XT, CPT> x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k + u * KL < ke) {
+        x[u] = ldx<XT, CPT, COH>(X + (int64_t)j[u] * C + c0);
+      } else {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) x[u].v[q] = (XT)0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) acc[q] = fma(m[u], (CT)x[u].v[q], acc[q]);
+    }
+  }
+}
+
+// The interface couplings of flagged row number f (A_out,i of eq.
+// "hL_splitting"; one value per block column).
+template <typename XT, typename CT, int CPT, bool COH>
+__device__ __forceinline__ void iface_row(const SpmmArgs& a, int f, int c0, CT (&acc)[CPT]) {
+  const CT* __restrict__ iv = static_cast<const CT*>(a.ival);
+  const XT* __restrict__ X = static_cast<const XT*>(a.X);
+  for (int ee = __ldg(a.iptr + f); ee < __ldg(a.iptr + f + 1); ++ee) {
+    const int j = __ldg(a.icol + ee);
+    const Vec<XT, CPT> xv = ldx<XT, CPT, COH>(X + (int64_t)j * a.C + c0);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int blk = (c0 + q) % a.nb;
+      acc[q] = fma(iv[(int64_t)ee * a.nb + blk], (CT)xv.v[q], acc[q]);
+    }
+  }
+}
+
+// Number of flagged rows before `row` (row <= rows).
+__device__ __forceinline__ int flag_index(const SpmmArgs& a, int row) {
+  if (row >= a.rows) return a.nflag;
+  const uint32_t wd = __ldg(a.imask + (row >> 5));
+  return __ldg(a.iprefix + (row >> 5)) + __popc(wd & ((1u << (row & 31)) - 1u));
+}
+
+// Epilogue of one row (entry lane 0): Y = alpha acc + beta Z, the optional dot.
+template <typename XT, typename OT, typename CT, typename DT, int CPT, bool HAS_DOT, bool COH>
+__device__ __forceinline__ void row_epilogue(const SpmmArgs& a, int row, int c0, CT (&acc)[CPT],
+                                             const Vec<XT, CPT>* zpre, DT (&dpart)[CPT]) {
+  const int C = a.C;
+  const CT alpha = (CT)a.alpha, beta = (CT)a.beta;
+  // Y may alias Z (in-place update z += ...); each row reads Z before writing Y.
+  OT* Y = static_cast<OT*>(a.Y);
+  Vec<OT, CPT> out;
+  if (a.beta != 0.0) {
+    const Vec<XT, CPT> zv = zpre ? *zpre : ldx<XT, CPT, COH>(static_cast<const XT*>(a.Z) + (int64_t)row * C + c0);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const CT y = fma(alpha, acc[q], beta * (CT)zv.v[q]);
+      out.v[q] = (OT)y;
+      acc[q] = y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const CT y = alpha * acc[q];
+      out.v[q] = (OT)y;
+      acc[q] = y;
+    }
+  }
+  stv<OT, CPT>(Y + (int64_t)row * C + c0, out);
+  if (HAS_DOT) {
+    if (a.dot.mode == DOT_WY) {
+      const Vec<XT, CPT> wv = ldx<XT, CPT, COH>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) dpart[q] = fma((DT)wv.v[q], (DT)acc[q], dpart[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) dpart[q] = fma((DT)acc[q], (DT)acc[q], dpart[q]);
+    }
+  }
+}
+
 // Rows [first_slot * rows_pb + k * slot_step * rows_pb, ...) below row_end
 // of one SpMM, for the whole block; this thread's dot partial (entry lane 0
 // only) is added to dpart.  Thread layout: a row is served by S = TPC * KL
@@ -171,10 +271,20 @@ __device__ __forceinline__ void dia_row(const SpmmArgs& a, int row, int c0, CT (
 // the long rows of the coarse levels over many lanes.  DIA: the matrix is in
 // the diagonal-offset form (one lane per row, no row pointers).  COH: vector
 // operands are loaded through L2 only (written earlier in the same launch).
+//
+// Interface rows (HAS_IFACE) take a second pass: the main pass computes
+// every row but stores none of the flagged ones, so no row waits on the
+// flag -> prefix -> pointer -> coupling chain; then the flagged rows (about
+// 2 % of them at 256^3) are recomputed with their couplings, from the
+// compact list of flagged rows.  whole: the block's share of the whole
+// matrix (the flagged rows slotted like the rows); otherwise the block owns
+// rows [first_slot * rows_pb, row_end) alone and takes their flagged rows.
+// A flagged row's sum is the same in both designs: its entries, then its
+// couplings (entry lane 0), then the lane combination.
 template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE, bool DIA = false,
           bool COH = false>
 __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int slot_step, int row_end,
-                                          typename AccOf<XT>::type (&dpart)[CPT]) {
+                                          typename AccOf<XT>::type (&dpart)[CPT], bool whole = true) {
   static_assert(!DIA || KL == 1, "the diagonal-offset form runs one entry lane per row");
   using CT = typename ComputeOf<MT, XT>::type;
   using DT = typename AccOf<XT>::type;  // per-thread dot partial type
@@ -191,14 +301,17 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
   const int e = KL > 1 ? w / TPC : 0;
   const int c0 = (w - e * TPC) * CPT;
   const bool slot_ok = g < rows_pb;
-  const MT* __restrict__ val = static_cast<const MT*>(a.val);
-  const XT* __restrict__ X = static_cast<const XT*>(a.X);
-  // Y may alias Z (in-place update z += ...); each row reads Z before writing Y.
   const XT* Z = static_cast<const XT*>(a.Z);
-  OT* Y = static_cast<OT*>(a.Y);
   const int32_t* __restrict__ ptr = a.ptr;
-  const int32_t* __restrict__ idx = a.idx;
-  const CT alpha = (CT)a.alpha, beta = (CT)a.beta;
+  auto lanes = [&](CT (&acc)[CPT]) {
+    if (KL > 1) {
+#pragma unroll
+      for (int off = KL / 2; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off * TPC);
+      }
+    }
+  };
 
   // The trip count is block-uniform (the shuffles need every lane of the warp).
   // In the variants with registers to spare (ZPF), the row pointers of a
@@ -230,96 +343,45 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
       kb = __ldg(ptr + row);
       ke = __ldg(ptr + row + 1);
     }
+    bool flagged = false;
     if (live) {
       // interface flag word and epilogue operand loaded with the row pointers,
       // off the critical path of the gathers
       const uint32_t iface_word = (HAS_IFACE && e == 0) ? __ldg(a.imask + (row >> 5)) : 0u;
       if (ZPF && e == 0 && a.beta != 0.0) zpre = ldx<XT, CPT, COH>(Z + (int64_t)row * C + c0);
-      if (DIA) dia_row<MT, XT, CT, CPT, COH>(a, row, c0, acc);
-      int k = DIA ? ke : kb + e;  // the diagonal form has no CSR entries
-      // U entries per step, predicated: all index/value loads first, then all
-      // gathers, so a row of up to U * KL entries costs one round trip and a
-      // 7-point row (U = 4) two, with every gather of a step in flight at once
-      constexpr int U = CPT >= 8 ? 2 : 4;
-      for (; k < ke; k += U * KL) {
-        int j[U];
-        CT m[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const bool ok = k + u * KL < ke;
-          j[u] = ok ? __ldg(idx + k + u * KL) : 0;
-          m[u] = ok ? cvt<CT>(val[k + u * KL]) : (CT)0;
-        }
-        Vec<XT, CPT> x[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (k + u * KL < ke) {
-            x[u] = ldx<XT, CPT, COH>(X + (int64_t)j[u] * C + c0);
-          } else {
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) x[u].v[q] = (XT)0;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-#pragma unroll
-          for (int q = 0; q < CPT; ++q) acc[q] = fma(m[u], (CT)x[u].v[q], acc[q]);
-        }
-      }
-      if (HAS_IFACE && e == 0) {
-        const uint32_t wd = iface_word;
-        const uint32_t bit = 1u << (row & 31);
-        if (wd & bit) {
-          const int f = __ldg(a.iprefix + (row >> 5)) + __popc(wd & (bit - 1u));
-          const CT* __restrict__ iv = static_cast<const CT*>(a.ival);
-          for (int ee = __ldg(a.iptr + f); ee < __ldg(a.iptr + f + 1); ++ee) {
-            const int j = __ldg(a.icol + ee);
-            const Vec<XT, CPT> xv = ldx<XT, CPT, COH>(X + (int64_t)j * C + c0);
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-              const int blk = (c0 + q) % a.nb;
-              acc[q] = fma(iv[(int64_t)ee * a.nb + blk], (CT)xv.v[q], acc[q]);
-            }
-          }
-        }
-      }
+      if (DIA)
+        dia_row<MT, XT, CT, CPT, COH>(a, row, c0, acc);
+      else
+        csr_row<MT, XT, CT, CPT, KL, COH>(a, kb, ke, e, c0, acc);
+      flagged = HAS_IFACE && (iface_word >> (row & 31)) & 1u;
     }
-    if (KL > 1) {
+    lanes(acc);
+    if (live && e == 0 && !flagged)
+      row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, ZPF && a.beta != 0.0 ? &zpre : nullptr,
+                                                      dpart);
+  }
+  if (HAS_IFACE) {
+    // the flagged rows, with their couplings
+    const int f_begin = whole ? 0 : flag_index(a, first_slot * rows_pb);
+    const int f_end = whole ? a.nflag : flag_index(a, row_end);
+    const int fs0 = whole ? first_slot : 0, fstep = whole ? slot_step : 1;
+    for (int fb = f_begin + fs0 * rows_pb; fb < f_end; fb += fstep * rows_pb) {
+      const int f = fb + g;
+      const bool live = slot_ok && f < f_end;
+      const int row = live ? __ldg(a.irows + f) : 0;
+      CT acc[CPT];
 #pragma unroll
-      for (int off = KL / 2; off >= 1; off >>= 1) {
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off * TPC);
-      }
-    }
-    if (live && e == 0) {
-      Vec<OT, CPT> out;
-      if (a.beta != 0.0) {
-        const Vec<XT, CPT> zv = ZPF ? zpre : ldx<XT, CPT, COH>(Z + (int64_t)row * C + c0);
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-          const CT y = fma(alpha, acc[q], beta * (CT)zv.v[q]);
-          out.v[q] = (OT)y;
-          acc[q] = y;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-          const CT y = alpha * acc[q];
-          out.v[q] = (OT)y;
-          acc[q] = y;
-        }
-      }
-      stv<OT, CPT>(Y + (int64_t)row * C + c0, out);
-      if (HAS_DOT) {
-        if (a.dot.mode == DOT_WY) {
-          const Vec<XT, CPT> wv = ldx<XT, CPT, COH>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
-#pragma unroll
-          for (int q = 0; q < CPT; ++q) dpart[q] = fma((DT)wv.v[q], (DT)acc[q], dpart[q]);
+      for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
+      if (live) {
+        if (DIA) {
+          dia_row<MT, XT, CT, CPT, COH>(a, row, c0, acc);
         } else {
-#pragma unroll
-          for (int q = 0; q < CPT; ++q) dpart[q] = fma((DT)acc[q], (DT)acc[q], dpart[q]);
+          csr_row<MT, XT, CT, CPT, KL, COH>(a, __ldg(ptr + row), __ldg(ptr + row + 1), e, c0, acc);
         }
+        if (e == 0) iface_row<XT, CT, CPT, COH>(a, f, c0, acc);
       }
+      lanes(acc);
+      if (live && e == 0) row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, nullptr, dpart);
     }
   }
 }
