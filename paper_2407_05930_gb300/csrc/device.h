@@ -146,6 +146,14 @@ struct SpmmArgs {
   int32_t doff[kMaxDiag] = {}, dsrc[kMaxDiag] = {}, dshift[kMaxDiag] = {};
   int64_t dstride = 0;
   const void* dval = nullptr;
+  // Diagonal-smoother epilogues (levels whose G is diagonal, jd = w g_ii^2,
+  // vector precision): jmode 1 also writes Y2 = jd o Y (presmoothing of the
+  // next level fused into its restriction); jmode 2 writes Y = X + jd o
+  // (alpha A X + beta Z) instead of the residual itself (postsmoothing fused
+  // into its residual; Y must not alias X).
+  int32_t jmode = 0;
+  const void* jd = nullptr;
+  void* Y2 = nullptr;
   DotArgs dot;
 };
 

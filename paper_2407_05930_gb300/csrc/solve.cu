@@ -626,20 +626,20 @@ void check_cycle_error(Device* D, cudaStream_t st) {
 // One V(nu, nu) cycle at level l: z = M_l^{-1} y (Alg. "apply" shape with the
 // A_inn hierarchy; presmoothing from zero).  `last` is the optional fused dot
 // of the final level-0 kernel.
-static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* last) {
+// The body of one V-cycle level, shared by vcycle() and the no-alloc
+// V-cycle (`lws`: the level work vectors; `sub`: the next level's cycle,
+// returning where it left z_{l+1}).  Returns the vector holding z on exit.
+// pre_done: z already holds the presmoothing from zero (written by the
+// restriction of the level above).  On a level whose G is diagonal the next
+// level's presmoothing is fused into this level's restriction, and (below
+// the finest level) the last postsmoothing into its residual, which then
+// writes the new z into lw.t: the diagonal steps cost no launch of their own.
+template <typename Sub>
+static const void* vcycle_level(const Ctx& c, std::vector<LevelWork>& lws, int l, const void* y, void* z,
+                                const DotArgs* last, bool pre_done, Sub&& sub) {
   Device* D = c.D;
   const DevLevel& L = D->lv[l];
-  PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
-  LevelWork& lw = W.lw[l];
-  if (c.fuse && l == D->fuse_level && !last) {
-    auto it = D->cycle_plans.find(cycle_key(c));
-    if (it != D->cycle_plans.end()) {
-      const CyclePlan& pl = it->second;
-      const cudaError_t e = launch_cycle(c.mt, c.vt, c.C, pl.grid, pl.phases, pl.nphases, D->bar, c.skip, c.st);
-      if (e != cudaSuccess) fail(AMGSYM_ERR_CUDA, std::string("coarse-cycle launch: ") + cudaGetErrorString(e));
-      return;
-    }
-  }
+  LevelWork& lw = lws[l];
   if (L.cinv) {
     launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st, c.skip);
     check_launch();
@@ -647,23 +647,70 @@ static void vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* l
       launch_dot(c.vt, L.n, c.C, last->W, z, *last, c.st, c.skip);
       check_launch();
     }
-    return;
+    return z;
   }
   const bool hat = c.finest_hat && l == 0;
   const ValType mt = c.mt;
   const VecType vt = c.vt;
   // presmoothing: the first sweep from zero is z = w G^T G y
-  smooth_first(c, L, lw, y, z);
+  if (!pre_done) smooth_first(c, L, lw, y, z);
   for (int k = 1; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, nullptr);
   // residual and restriction r_c = P^T (y - A z)
   spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
-  LevelWork& cw = W.lw[l + 1];
-  spmm(c, L.R, mt, vt, vt, lw.r, cw.y, 1.0, 0.0, nullptr, false, nullptr);
-  vcycle(c, l + 1, cw.y, cw.z, nullptr);
+  LevelWork& cw = lws[l + 1];
+  const DevLevel& Lc = D->lv[l + 1];
+  const bool persist_next = c.fuse && l + 1 == D->fuse_level;
+  const bool fuse_pre = Lc.jd(vt) && !Lc.cinv && !persist_next;
+  {
+    SpmmArgs a = make_spmm_args(c, L.R, mt, vt, vt, lw.r, cw.y, 1.0, 0.0, nullptr, false, nullptr);
+    if (fuse_pre) {
+      a.jmode = 1;
+      a.jd = Lc.jd(vt);
+      a.Y2 = cw.z;
+    }
+    launch_spmm(mt, vt, vt, a, c.st);
+    check_launch();
+  }
+  const void* zc = sub(l + 1, cw.y, cw.z, fuse_pre);
   // prolongation and update z += P z_c
-  spmm(c, L.P, mt, vt, vt, cw.z, z, 1.0, 1.0, z, false, nullptr);
+  spmm(c, L.P, mt, vt, vt, zc, z, 1.0, 1.0, z, false, nullptr);
   // postsmoothing
-  for (int k = 0; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, k == D->nu - 1 ? last : nullptr);
+  const void* jd = L.jd(vt);
+  const bool fuse_post = jd && l > 0 && !(last && D->nu >= 1);
+  for (int k = 0; k < D->nu; ++k) {
+    const bool fin = k == D->nu - 1;
+    if (fin && fuse_post) {
+      SpmmArgs a = make_spmm_args(c, L.A, mt, vt, vt, z, lw.t, -1.0, 1.0, y, hat, nullptr);
+      a.jmode = 2;
+      a.jd = jd;
+      launch_spmm(mt, vt, vt, a, c.st);
+      check_launch();
+      return lw.t;
+    }
+    smooth_sweep(c, L, lw, y, z, hat, fin ? last : nullptr);
+  }
+  return z;
+}
+
+// One V(nu, nu) cycle at level l: z = M_l^{-1} y (Alg. "apply" shape with the
+// A_inn hierarchy; presmoothing from zero).  `last` is the optional fused dot
+// of the final level-0 kernel.  Returns the vector that holds z_l on exit
+// (z, or the level's t after a fused diagonal postsmoothing, never at l = 0).
+static const void* vcycle(const Ctx& c, int l, const void* y, void* z, const DotArgs* last, bool pre_done = false) {
+  Device* D = c.D;
+  PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
+  if (c.fuse && l == D->fuse_level && !last) {
+    auto it = D->cycle_plans.find(cycle_key(c));
+    if (it != D->cycle_plans.end()) {
+      const CyclePlan& pl = it->second;
+      const cudaError_t e = launch_cycle(c.mt, c.vt, c.C, pl.grid, pl.phases, pl.nphases, D->bar, c.skip, c.st);
+      if (e != cudaSuccess) fail(AMGSYM_ERR_CUDA, std::string("coarse-cycle launch: ") + cudaGetErrorString(e));
+      return z;
+    }
+  }
+  return vcycle_level(c, W.lw, l, y, z, last, pre_done, [&](int l1, const void* y1, void* z1, bool pd) {
+    return vcycle(c, l1, y1, z1, nullptr, pd);
+  });
 }
 
 DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb,
@@ -1098,26 +1145,10 @@ void* noalloc_scratch(int dev) {
 }
 
 // The V-cycle of vcycle() above with caller-provided level buffers.
-void vcycle_with(const Ctx& c, std::vector<LevelWork>& lws, int l, const void* y, void* z) {
-  Device* D = c.D;
-  const DevLevel& L = D->lv[l];
-  LevelWork& lw = lws[l];
-  if (L.cinv) {
-    launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st, c.skip);
-    check_launch();
-    return;
-  }
-  const bool hat = c.finest_hat && l == 0;
-  const ValType mt = c.mt;
-  const VecType vt = c.vt;
-  smooth_first(c, L, lw, y, z);
-  for (int k = 1; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, nullptr);
-  spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
-  LevelWork& cw = lws[l + 1];
-  spmm(c, L.R, mt, vt, vt, lw.r, cw.y, 1.0, 0.0, nullptr, false, nullptr);
-  vcycle_with(c, lws, l + 1, cw.y, cw.z);
-  spmm(c, L.P, mt, vt, vt, cw.z, z, 1.0, 1.0, z, false, nullptr);
-  for (int k = 0; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, nullptr);
+const void* vcycle_with(const Ctx& c, std::vector<LevelWork>& lws, int l, const void* y, void* z, bool pre_done) {
+  return vcycle_level(c, lws, l, y, z, nullptr, pre_done, [&](int l1, const void* y1, void* z1, bool pd) {
+    return vcycle_with(c, lws, l1, y1, z1, pd);
+  });
 }
 
 }  // namespace
@@ -1171,7 +1202,7 @@ extern "C" amgsym_status amgsym_vcycle_noalloc(amgsym_t h, const void* R_dev, vo
     }
   }
   Ctx c{D, C, vt, mt, finest_hat != 0, (cudaStream_t)stream};
-  vcycle_with(c, lws, 0, R_dev, Z_dev);
+  vcycle_with(c, lws, 0, R_dev, Z_dev, false);
   API_END
 }
 

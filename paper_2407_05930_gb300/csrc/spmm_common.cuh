@@ -247,6 +247,21 @@ __device__ __forceinline__ void row_epilogue(const SpmmArgs& a, int row, int c0,
       acc[q] = y;
     }
   }
+  if (a.jmode == 1) {
+    // presmoothing of the next level from zero: Y2 = jd o Y, the arithmetic
+    // of the stand-alone diagonal step (one product of the stored values)
+    const XT d = static_cast<const XT*>(a.jd)[row];
+    Vec<OT, CPT> o2;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) o2.v[q] = (OT)(d * (XT)out.v[q]);
+    stv<OT, CPT>(static_cast<OT*>(a.Y2) + (int64_t)row * C + c0, o2);
+  } else if (a.jmode == 2) {
+    // postsmoothing: X + jd o r with r the stored residual value
+    const XT d = static_cast<const XT*>(a.jd)[row];
+    const Vec<XT, CPT> xr = ldx<XT, CPT, COH>(static_cast<const XT*>(a.X) + (int64_t)row * C + c0);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) out.v[q] = (OT)fma(d, (XT)out.v[q], xr.v[q]);
+  }
   stv<OT, CPT>(Y + (int64_t)row * C + c0, out);
   if (HAS_DOT) {
     if (a.dot.mode == DOT_WY) {
