@@ -40,9 +40,9 @@ METRIC = "AMG-PCG solves/s + SpMM HBM GB/s, 256^3 s=3, mixed vs FP64 at rel-res 
 # the reduced SpMM on this workload, from an ncu capture of the kernel sources
 # with this SHA-256 (profiles/spmm_reduced_fp32_256cube_s3.md).  Reported as
 # roofline.traffic only while the sources are unchanged.
-SPMM_TRAFFIC_BYTES = 140.9e6
+SPMM_TRAFFIC_BYTES = 152.2e6
 SPMM_SOURCES = ("paper_2407_05930_gb300/csrc/k_spmm.cu", "paper_2407_05930_gb300/csrc/spmm_common.cuh")
-SPMM_SOURCES_SHA256 = "16b0cfc6117a47d29d644930852bb4c7cbcf25f40e3dac583b799493e9a2d628"
+SPMM_SOURCES_SHA256 = "6f21e8049d657ebfb1561ca16bfa1536f1a631888c803285fb6fa1b1ed3086a2"
 
 
 def _spmm_sources_sha():
