@@ -126,7 +126,7 @@ typedef struct {
   int32_t use_x0;      /* 1: x_dev holds the initial guess; 0: start from zero */
   double inner_tol;    /* mixed: floor of the inner PCG relative reduction per
                           refinement step; the target of step k is
-                          clamp(tol / (4 relres_k), inner_tol, 0.5), 1e-6 */
+                          clamp(tol / (4 relres_k), inner_tol, 0.5), 3e-7 */
   int32_t max_outer;   /* mixed: refinement steps, 20 */
   int32_t finest_hat;  /* 1: V-cycle finest-level residuals use A^_i instead of A_inn */
   int32_t use_graph;   /* 1: capture one PCG iteration in a CUDA graph and replay it */

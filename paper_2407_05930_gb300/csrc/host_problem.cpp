@@ -70,7 +70,7 @@ extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {
   o->maxit = 500;
   o->precision = AMGSYM_PREC_FP64;
   o->use_x0 = 0;
-  o->inner_tol = 1e-6;
+  o->inner_tol = 3e-7;
   o->max_outer = 20;
   o->finest_hat = 0;
   o->use_graph = 1;

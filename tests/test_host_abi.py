@@ -212,3 +212,26 @@ def test_diagonal_form_detection(N, s):
     assert amg.lib.amgsym_level_dia(P._h, 0, 1, None, None, None) == -1  # P has no diagonal form
     with pytest.raises(amg.AmgsymError):
         P.level_dia(P.num_levels(), "A")
+
+
+def test_coarse_levels_take_a_diagonal_fsai_factor():
+    """fsai_max_lower_coarse: the finest level keeps the 4-entry lower FSAI
+    pattern of a 7-point stencil, every coarse level a diagonal one (damped
+    Jacobi with the same omega rule); with 4 the coarse factors are not
+    diagonal.  A diagonal G is D^{-1/2}-like: positive, so G^T G is SPD."""
+    N, s = (24, 20, 16), 2
+    g = gaussian_logk(N, s, seed=6, corr=2.0)
+    P = amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, coarse_max=32)
+    assert P.num_levels() >= 3
+    rp, ci, v, shape = P.level_matrix(0, "G")
+    assert np.max(np.diff(rp)) == 4
+    for l in range(1, P.num_levels() - 1):
+        rp, ci, v, shape = P.level_matrix(l, "G")
+        rows = np.arange(shape[0])
+        assert np.array_equal(np.diff(rp), np.ones(shape[0], dtype=np.int64))
+        assert np.array_equal(ci, rows) and np.all(v > 0)
+    Q = amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, coarse_max=32, fsai_max_lower_coarse=4)
+    rp, ci, v, shape = Q.level_matrix(1, "G")
+    assert np.max(np.diff(rp)) > 1
+    with pytest.raises(amg.AmgsymError):
+        amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, fsai_max_lower_coarse=0)
