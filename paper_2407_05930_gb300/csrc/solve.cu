@@ -318,7 +318,6 @@ Tile fixed_tile(const DevCsr& M, int32_t C, VecType xt) {
   return t;
 }
 
-int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt) { return fixed_tile(M, C, xt).kl; }
 
 SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X,
                         void* Y, double alpha, double beta, const void* Z, bool iface, const DotArgs* dot) {

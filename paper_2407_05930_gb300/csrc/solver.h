@@ -127,7 +127,6 @@ void check_cycle_error(Device* D, cudaStream_t st);
 
 void ensure_work(Device* D, int32_t nrhs, VecType vt);
 void tune_tiles(const Ctx& c);
-int32_t entry_lanes(const DevCsr& M, int32_t C, VecType xt);
 Tile fixed_tile(const DevCsr& M, int32_t C, VecType xt);
 SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X,
                         void* Y, double alpha, double beta, const void* Z, bool iface, const DotArgs* dot);
