@@ -11,8 +11,9 @@ FP32 values and vectors) is timed on its own for the roofline entry.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-N > 1 runs N independent replicas (the solve does not shard; see DESIGN),
-one per rank under torch.distributed; rank 0 prints one JSON line.
+N > 1 runs N independent replicas (one problem is solved on one GPU: the
+solve has no data-path exchange to shard), one per rank under
+torch.distributed; rank 0 prints one JSON line.
 """
 
 from __future__ import annotations
