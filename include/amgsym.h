@@ -183,6 +183,17 @@ amgsym_status amgsym_problem_sizes(amgsym_t h, int64_t* n, int64_t* n_b, int32_t
 amgsym_status amgsym_get_inner_block(amgsym_t h, int64_t* rowptr, int32_t* colidx, double* vals);
 amgsym_status amgsym_get_interface(amgsym_t h, int32_t* row, int32_t* col, double* vals);
 
+/* New values for the same operator pattern (a new coefficient field k, as
+ * in the adjoint's outer loop): vals host FP64 [nnz] in the order of the
+ * colidx passed to amgsym_create_problem (the handle keeps that pattern: 8
+ * bytes per row and 4 per stored entry).  The values are validated as in
+ * amgsym_create_problem (block structure of eq. "struct_2sym", symmetry,
+ * positive diagonal); a rejected update returns the same errors and leaves
+ * the problem unchanged.  An accepted one replaces A_inn and the interface
+ * couplings and releases the hierarchy and the device copies: call
+ * amgsym_setup before the next solve (AMGSYM_ERR_STATE otherwise). */
+amgsym_status amgsym_update_values(amgsym_t h, const double* vals);
+
 /* ------------------------------------------------------------------------
  * Setup: AMG hierarchy of A_inn on the host (PMIS, extended+i interpolation
  * truncated, Galerkin R A P with R = P^T, static FSAI on the strongest lower

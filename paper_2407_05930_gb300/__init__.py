@@ -107,6 +107,7 @@ def _load():
         "amgsym_solve_opts_default": (None, [ctypes.POINTER(SolveOpts)]),
         "amgsym_last_error": (ctypes.c_char_p, []),
         "amgsym_create_problem": (i32, [i64, pi64, pi32, pdbl, i32, pi32, ctypes.POINTER(P)]),
+        "amgsym_update_values": (i32, [P, pdbl]),
         "amgsym_problem_sizes": (i32, [P, pi64, pi64, pi32, pi64, pi64, pi64]),
         "amgsym_get_inner_block": (i32, [P, pi64, pi32, pdbl]),
         "amgsym_get_interface": (i32, [P, pi32, pi32, pdbl]),
@@ -149,7 +150,7 @@ lib = _load()
 EXPORTED = [
     name
     for name in (
-        "amgsym_opts_default amgsym_solve_opts_default amgsym_last_error amgsym_create_problem "
+        "amgsym_opts_default amgsym_solve_opts_default amgsym_last_error amgsym_create_problem amgsym_update_values "
         "amgsym_problem_sizes amgsym_get_inner_block amgsym_get_interface amgsym_setup "
         "amgsym_num_levels amgsym_level_sizes amgsym_get_level_matrix amgsym_solve "
         "amgsym_solve_adjoint amgsym_transform_forward amgsym_transform_backward "
@@ -310,6 +311,13 @@ class Problem:
         _check(lib.amgsym_get_interface(self._h, _ptr(r, ctypes.c_int32), _ptr(c, ctypes.c_int32),
                                         _ptr(v, ctypes.c_double)))
         return r[:ne], c[:ne], v[: ne * self.nb].reshape(ne, self.nb)
+
+    def update_values(self, vals):
+        """New FP64 values for the pattern given at creation (amgsym_update_values);
+        the hierarchy is released: call setup() again before solving."""
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        _check(lib.amgsym_update_values(self._h, _ptr(vals, ctypes.c_double)))
+        return self
 
     def setup(self, **kw):
         o = default_opts(**kw)

@@ -80,18 +80,19 @@ extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {
 // Sign of entry (i, j) of the Sylvester-Hadamard matrix 2^{s/2} P_s (eq. "P_s").
 static inline double hsign(int i, int j) { return (__builtin_popcount((unsigned)(i & j)) & 1) ? -1.0 : 1.0; }
 
-extern "C" amgsym_status amgsym_create_problem(int64_t n, const int64_t* rowptr,
-                                               const int32_t* colidx, const double* vals,
-                                               int32_t s, const int32_t* perm, amgsym_t* out) {
-  API_BEGIN
-  if (!out) fail(AMGSYM_ERR_ARG, "out is NULL");
-  *out = nullptr;
-  if (!rowptr || !colidx || !vals || !perm) fail(AMGSYM_ERR_ARG, "NULL input array");
-  if (n <= 0) fail(AMGSYM_ERR_ARG, "n must be positive");
-  if (s < 0 || s > 10) fail(AMGSYM_ERR_ARG, "s out of range [0, 10]");
+// The blocks of a full operator in mirrored order (Sec. 2): A_inn = H_0 and
+// the interface couplings A_out,i, after validating the CSR, the map, the
+// block structure of eq. "struct_2sym", symmetry and the diagonal.  Throws
+// (through fail) on any violation; nothing is modified then.
+struct Blocks {
+  Csr Ainn;
+  std::vector<int32_t> irow, icol;
+  std::vector<double> ivals;
+};
+
+static Blocks extract_blocks(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* vals,
+                             int32_t s, const int32_t* perm) {
   const int32_t nb = 1 << s;
-  if (n % nb) fail(AMGSYM_ERR_MAP, "n is not divisible by 2^s");
-  if (n / nb > INT32_MAX - 1) fail(AMGSYM_ERR_ARG, "base block too large for 32-bit indices");
   const int64_t n_b = n / nb;
   // CSR sanity.
   if (rowptr[0] != 0) fail(AMGSYM_ERR_ARG, "rowptr[0] != 0");
@@ -189,14 +190,7 @@ extern "C" amgsym_status amgsym_create_problem(int64_t n, const int64_t* rowptr,
       fail(AMGSYM_ERR_NOT_SPD, "non-positive or missing diagonal entry");
   }
 
-  auto* P = new amgsym_problem();
-  std::unique_ptr<amgsym_problem> guard(P);
-  P->n = n;
-  P->n_b = n_b;
-  P->s = s;
-  P->nb = nb;
-  P->Ainn = std::move(Hm[0]);
-  P->perm.assign(perm, perm + n);
+  Blocks B;
   // Interface couplings A_out,i = sum_{m>=1} sign(i, m) H_m (eq. "hL_splitting").
   for (int64_t l = 0; l < n_b; ++l) {
     std::vector<int32_t> cols;
@@ -205,20 +199,67 @@ extern "C" amgsym_status amgsym_create_problem(int64_t n, const int64_t* rowptr,
     std::sort(cols.begin(), cols.end());
     cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
     for (int32_t c : cols) {
-      P->irow.push_back((int32_t)l);
-      P->icol.push_back(c);
+      B.irow.push_back((int32_t)l);
+      B.icol.push_back(c);
       for (int32_t i = 0; i < nb; ++i) {
         double acc = 0.0;
         for (int32_t m = 1; m < nb; ++m) {
           double v;
           if (lookup(Hm[m], l, c, &v)) acc += hsign(i, m) * v;
         }
-        P->ivals.push_back(acc);
+        B.ivals.push_back(acc);
       }
     }
   }
+  B.Ainn = std::move(Hm[0]);
+  return B;
+}
+
+extern "C" amgsym_status amgsym_create_problem(int64_t n, const int64_t* rowptr,
+                                               const int32_t* colidx, const double* vals,
+                                               int32_t s, const int32_t* perm, amgsym_t* out) {
+  API_BEGIN
+  if (!out) fail(AMGSYM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!rowptr || !colidx || !vals || !perm) fail(AMGSYM_ERR_ARG, "NULL input array");
+  if (n <= 0) fail(AMGSYM_ERR_ARG, "n must be positive");
+  if (s < 0 || s > 10) fail(AMGSYM_ERR_ARG, "s out of range [0, 10]");
+  const int32_t nb = 1 << s;
+  if (n % nb) fail(AMGSYM_ERR_MAP, "n is not divisible by 2^s");
+  if (n / nb > INT32_MAX - 1) fail(AMGSYM_ERR_ARG, "base block too large for 32-bit indices");
+  Blocks B = extract_blocks(n, rowptr, colidx, vals, s, perm);
+  auto* P = new amgsym_problem();
+  std::unique_ptr<amgsym_problem> guard(P);
+  P->n = n;
+  P->n_b = n / nb;
+  P->s = s;
+  P->nb = nb;
+  P->Ainn = std::move(B.Ainn);
+  P->irow = std::move(B.irow);
+  P->icol = std::move(B.icol);
+  P->ivals = std::move(B.ivals);
+  P->perm.assign(perm, perm + n);
+  // the pattern, for amgsym_update_values
+  P->full_ptr.assign(rowptr, rowptr + n + 1);
+  P->full_idx.assign(colidx, colidx + rowptr[n]);
   amgsym_opts_default(&P->opts);
   *out = guard.release();
+  API_END
+}
+
+extern "C" amgsym_status amgsym_update_values(amgsym_t h, const double* vals) {
+  API_BEGIN
+  if (!h) fail(AMGSYM_ERR_ARG, "NULL handle");
+  if (!vals) fail(AMGSYM_ERR_ARG, "NULL vals");
+  // validate and extract first: a rejected update leaves the problem as it was
+  Blocks B = extract_blocks(h->n, h->full_ptr.data(), h->full_idx.data(), vals, h->s, h->perm.data());
+  device_free(h);
+  h->have_hierarchy = false;
+  h->H = HostHierarchy();
+  h->Ainn = std::move(B.Ainn);
+  h->irow = std::move(B.irow);
+  h->icol = std::move(B.icol);
+  h->ivals = std::move(B.ivals);
   API_END
 }
 

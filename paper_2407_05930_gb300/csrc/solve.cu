@@ -618,7 +618,7 @@ void check_cycle_error(Device* D, cudaStream_t st) {
   CK(cudaStreamSynchronize(st));
   if (err) {
     CK(cudaMemset(D->bar.count, 0, 4 * sizeof(unsigned)));
-    fail(AMGSYM_ERR_CUDA, "coarse-cycle kernel: a grid-barrier wait ran out (the launch stopped early)");
+    fail(AMGSYM_ERR_DEVICE_TIMEOUT, "coarse-cycle kernel: a grid-barrier wait ran out (the launch stopped early)");
   }
 }
 

@@ -235,3 +235,43 @@ def test_coarse_levels_take_a_diagonal_fsai_factor():
     assert np.max(np.diff(rp)) > 1
     with pytest.raises(amg.AmgsymError):
         amg.Problem.structured(N, 1.5, g, s).setup(host_only=1, fsai_max_lower_coarse=0)
+
+
+@pytest.mark.parametrize("N,s", [((8, 6, 4), 3), ((10, 6), 1)])
+def test_update_values_replaces_blocks_and_rejects_broken_symmetry(N, s):
+    """amgsym_update_values: a new coefficient field on the same pattern gives
+    exactly the oracle's blocks of the new operator; values that break the
+    block structure are rejected and leave the problem as it was; an
+    accepted update drops the hierarchy until the next setup."""
+    h = grid.widths(N, 1.5)
+    perm = symmetry.mirror_perm(N, s)
+    g1 = gaussian_logk(N, s, seed=8, corr=2.0)
+    g2 = gaussian_logk(N, s, seed=9, corr=2.0)
+    A1 = fv.assemble(h, np.exp(g1))
+    A2 = fv.assemble(h, np.exp(g2))
+    assert np.array_equal(A1.indptr, A2.indptr) and np.array_equal(A1.indices, A2.indices)
+    P = amg.Problem(A1.shape[0], A1.indptr, A1.indices, A1.data, s, perm)
+    P.setup(host_only=1, coarse_max=16)
+    assert P.num_levels() >= 2
+    P.update_values(A2.data)
+    assert P.num_levels() == 0  # hierarchy released
+    rp, ci, v = P.inner_block()
+    Ainn = sp.csr_matrix((v, ci, rp), shape=(P.n_b, P.n_b))
+    H = symmetry.blocks(A2, perm)
+    assert (Ainn != H[0]).nnz == 0
+    r, c, iv = P.interface()
+    hat = transform.hat_blocks_sparse(H)
+    for i in range(1 << s):
+        Aout = sp.csr_matrix((iv[:, i], (r, c)), shape=Ainn.shape)
+        assert abs(Aout - (hat[i] - H[0])).max() <= 1e-15 * abs(H[0]).max()
+    # one entry of one mirror copy changed: rejected, nothing modified
+    bad = A1.data.copy()
+    p = perm[1, 5] if s > 0 else 5
+    bad[A1.indptr[p]] *= 1.5
+    with pytest.raises(amg.AmgsymError) as e:
+        P.update_values(bad)
+    assert e.value.name == "ERR_NOT_SYMMETRIC"
+    rp2, ci2, v2 = P.inner_block()
+    assert np.array_equal(v2, v) and np.array_equal(ci2, ci)
+    P.setup(host_only=1, coarse_max=16)
+    assert P.num_levels() >= 2
