@@ -299,9 +299,13 @@ amgsym_status amgsym_cycle_timeout_check(amgsym_t h, int32_t nrhs, int32_t prec,
  * The level vectors come from one fixed array of 32 MiB (33554432 bytes) in
  * device global memory, declared statically in the library; every GPU that
  * loads the library holds it until the process exits.  A problem whose
- * V-cycle needs more (sum over levels of 2 or 4 vectors of n_l x nrhs*2^s
+ * V-cycle needs more is rejected with AMGSYM_ERR_ARG and a message giving
+ * both sizes.  The need is a sum over levels of vectors of n_l x nrhs*2^s
  * values, 8 bytes each in FP64 and 4 in the mixed modes, each rounded up to
- * 256 bytes) is rejected with AMGSYM_ERR_ARG and a message giving both sizes.
+ * 256 bytes: 2 vectors on the finest level (residual, smoother temporary),
+ * 4 on every other level (right-hand side, solution, residual, temporary),
+ * and 2 on the dense coarsest level (right-hand side, solution) -- none when
+ * the finest level is itself the coarsest.
  * The entry point calls no cudaMalloc, cudaFree or other allocating routine.
  * Its first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress) and caches it; make that first call
@@ -356,7 +360,13 @@ amgsym_status amgsym_fv_grad_logk(int32_t d, const int64_t* N, const double* wid
  * amgsym_batch_create: a batch over `count` problems that are already set up
  * on one device (amgsym_setup, hierarchies of at least two levels, the same
  * nu), with nrhs[p] right-hand sides for problem p (nrhs[p] * 2^s_p <= 256).
- * The batch references the problems; they must outlive it.
+ * The batch references the problems; they must outlive it.  A problem of
+ * the batch may be given new values and set up again (amgsym_update_values,
+ * amgsym_setup): that frees the device copies the batch's launch plans and
+ * captured graph point to, and the next amgsym_batch_solve notices it and
+ * rebuilds them (a process-wide generation count identifies every device
+ * copy).  If the problem no longer meets the conditions above (a single-level
+ * hierarchy, another nu or device), that solve returns AMGSYM_ERR_STATE.
  *
  * amgsym_batch_solve: solves every problem (Alg. 1 per problem) with the
  * mixed-precision refinement of amgsym_solve (sopts->precision must be

@@ -56,7 +56,10 @@ struct Batch {
   std::vector<DevScalars> sc_in, sc_out;
   std::vector<BLaunch> plan_iter, plan_start, plan_resid;
   int planned_key = -1;
-  std::vector<uint64_t> planned_gen;  // work generations the plans were built on
+  // (Device epoch, work generation) of every problem when the plans were
+  // built: the plans and the graph hold that Device's matrix and work
+  // pointers, which amgsym_update_values / amgsym_setup free
+  std::vector<uint64_t> planned_gen;
   cudaGraphExec_t graph = nullptr;
   int64_t graph_kernels = 0;
   cudaStream_t cap_stream = nullptr;
@@ -579,6 +582,15 @@ static amgsym_status batch_solve_impl(Batch* B, const double* const* b_dev, doub
   std::vector<Ctx> ctx(n);
   for (int p = 0; p < n; ++p) {
     Device* D = require_dev(B->probs[p]);
+    // the conditions of amgsym_batch_create, again: a problem may have been
+    // set up anew since (amgsym_update_values + amgsym_setup)
+    if (D->device_id != B->device_id)
+      fail(AMGSYM_ERR_STATE, "problem " + std::to_string(p) + " is no longer on the batch's device");
+    if (D->lv.size() < 2)
+      fail(AMGSYM_ERR_STATE, "problem " + std::to_string(p) + " now has a single-level hierarchy");
+    if (D->nu != require_dev(B->probs[0])->nu)
+      fail(AMGSYM_ERR_STATE, "the problems of a batch must use the same nu");
+    BCK(cudaSetDevice(B->device_id));
     if (!b_dev[p] || !x_dev[p]) fail(AMGSYM_ERR_ARG, "NULL vector for problem " + std::to_string(p));
     if (!(B->probs[p]->opts.precisions & (vmt == VAL_BF16 ? 4 : 2)))
       fail(AMGSYM_ERR_STATE, "problem " + std::to_string(p) + " was set up without the value precision of this mode");
@@ -600,9 +612,15 @@ static amgsym_status batch_solve_impl(Batch* B, const double* const* b_dev, doub
     B->sc_out[p].tol2 = B->tol2_out + p;
   }
   const int key = (vmt == VAL_BF16 ? 2 : 1) | (o.finest_hat ? 4 : 0);
-  std::vector<uint64_t> gens(n);
-  for (int p = 0; p < n; ++p) gens[p] = ctx[p].D->work_gen;
-  if (B->planned_key != key || B->planned_gen != gens) {
+  auto generations = [&]() {
+    std::vector<uint64_t> g(2 * (size_t)n);
+    for (int p = 0; p < n; ++p) {
+      g[2 * p] = ctx[p].D->epoch;
+      g[2 * p + 1] = ctx[p].D->work_gen;
+    }
+    return g;
+  };
+  if (B->planned_key != key || B->planned_gen != generations()) {
     B->tune = o.tune != 0;
     B->tuned.clear();
     BCK(cudaStreamSynchronize(st));  // no earlier work of this batch in flight
@@ -618,8 +636,7 @@ static amgsym_status batch_solve_impl(Batch* B, const double* const* b_dev, doub
       BCK(cudaMemset(B->status_in, 0, sizeof(int32_t) * 4 * n));
       B->tune = false;
     }
-    for (int p = 0; p < n; ++p) gens[p] = ctx[p].D->work_gen;  // tuning allocates nothing, but be exact
-    B->planned_gen = gens;
+    B->planned_gen = generations();  // tuning allocates nothing, but be exact
   }
   // forward transforms, norms, initial state (per problem; outside the loop)
   for (int p = 0; p < n; ++p) {

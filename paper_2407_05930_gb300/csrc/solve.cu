@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -22,6 +23,11 @@
 #include "solver.h"
 
 namespace amgsym {
+
+uint64_t next_generation() {
+  static std::atomic<uint64_t> counter{0};
+  return ++counter;
+}
 
 void check_launch() {
   cudaError_t e = cudaGetLastError();
@@ -128,6 +134,7 @@ void device_upload(amgsym_problem* p) {
   device_free(p);
   auto* D = new Device();
   p->dev = D;
+  D->epoch = next_generation();
   CK(cudaGetDevice(&D->device_id));
   D->precisions = p->opts.precisions | 1;  // FP64 operator always (outer residuals)
   D->nu = p->opts.nu;
@@ -241,7 +248,7 @@ void ensure_work(Device* D, int32_t nrhs, VecType vt) {
   if (nrhs > D->work_nrhs) {
     CK(cudaDeviceSynchronize());
     free_work(D);
-    D->work_gen++;
+    D->work_gen = next_generation();
     D->work_nrhs = nrhs;
     const int32_t C = nrhs * D->nb;
     D->bh = dalloc<double>(D->work_owned, D->n_b * C);
@@ -253,7 +260,7 @@ void ensure_work(Device* D, int32_t nrhs, VecType vt) {
   }
   PrecWork& W = vt == VEC_F64 ? D->w64 : D->w32;
   if (W.ready) return;
-  D->work_gen++;
+  D->work_gen = next_generation();
   const int32_t C = D->work_nrhs * D->nb;
   const size_t es = vt == VEC_F64 ? 8 : 4;
   auto vec = [&](int64_t rows) -> void* {
@@ -1165,8 +1172,10 @@ extern "C" amgsym_status amgsym_vcycle_noalloc(amgsym_t h, const void* R_dev, vo
   const ValType mt = f64 ? VAL_F64 : prec == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : VAL_F32;
   const int32_t C = nrhs * D->nb;
   const size_t es = f64 ? 8 : 4;
-  // Carve the level vectors (r, t on every level; y, z below the finest)
-  // from the fixed scratch, each 256-byte aligned.
+  // Carve the level vectors from the fixed scratch, each 256-byte aligned:
+  // y, z below the finest level (the level's right-hand side and solution);
+  // r, t on every level that smooths (the dense coarsest solve reads y and
+  // writes z only).
   std::vector<size_t> off;
   size_t need = 0;
   auto take = [&](int64_t rows) {
@@ -1175,8 +1184,10 @@ extern "C" amgsym_status amgsym_vcycle_noalloc(amgsym_t h, const void* R_dev, vo
   };
   for (size_t l = 0; l < D->lv.size(); ++l) {
     const int64_t n = D->lv[l].n;
-    take(n);  // r
-    take(n);  // t
+    if (!D->lv[l].cinv) {
+      take(n);  // r
+      take(n);  // t
+    }
     if (l > 0) {
       take(n);  // y
       take(n);  // z
@@ -1193,8 +1204,10 @@ extern "C" amgsym_status amgsym_vcycle_noalloc(amgsym_t h, const void* R_dev, vo
   std::vector<LevelWork> lws(D->lv.size());
   size_t k = 0;
   for (size_t l = 0; l < D->lv.size(); ++l) {
-    lws[l].r = base + off[k++];
-    lws[l].t = base + off[k++];
+    if (!D->lv[l].cinv) {
+      lws[l].r = base + off[k++];
+      lws[l].t = base + off[k++];
+    }
     if (l > 0) {
       lws[l].y = base + off[k++];
       lws[l].z = base + off[k++];

@@ -71,9 +71,17 @@ struct Tile {
 };
 using TileKey = std::tuple<const void*, int32_t, int, int, int>;  // matrix idx array, C, mt, xt, ot
 
+// Generations come from one process-wide counter that only goes up, so a
+// value identifies one Device object and one set of its work arrays for the
+// life of the process: a Device created after another was freed never
+// repeats its generations (a batch compares them to decide whether its plans,
+// which hold device pointers, are still valid).
+uint64_t next_generation();
+
 struct Device {
   int device_id = 0;
-  uint64_t work_gen = 0;   // bumped whenever work arrays are (re)allocated
+  uint64_t epoch = 0;      // next_generation() at upload: identifies this Device
+  uint64_t work_gen = 0;   // next_generation() whenever work arrays are (re)allocated
   uint64_t tiles_gen = 0;  // bumped whenever the tuner changes tiles
   std::map<TileKey, Tile> tiles;
   std::set<std::tuple<int32_t, int, int>> tuned;  // (C, vt, mt) already tuned

@@ -86,3 +86,46 @@ def test_adjoint_full_size_192cube_mixed():
     # gradient formula applied by the oracle to the GPU's u and lambda
     ref = adjoint.grad_logk(h, k, uu, lam)
     assert np.linalg.norm(dg - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_second_forward_reuses_the_handle():
+    """An optimisation loop: two forwards with different fields on one
+    SymPoisson create one problem (the second field goes through
+    amgsym_update_values), and both gradients match the oracle's."""
+    from paper_2407_05930_gb300.autograd import SymPoisson
+
+    N, s, gamma = (32, 32, 32), 3, 1.5
+    op = SymPoisson(N, gamma, s, solve_kw=dict(tol=1e-12, precision=amg.PREC_FP64))
+    n = int(np.prod(N))
+    b = rhs_uniform(n, 1, config=5)[0]
+    ut = u_target(n)
+    h = grid.widths(N, gamma)
+    handle = None
+    for seed in (5, 6):
+        g = gaussian_logk(N, s, seed=seed, corr=3.0)
+        bt = torch.from_numpy(b).to(DEV).requires_grad_(True)
+        gt = torch.from_numpy(g).to(DEV).requires_grad_(True)
+        u = op(bt, gt)
+        L = torch.sum((u - torch.from_numpy(ut).to(DEV)) ** 2)
+        L.backward()
+        if handle is None:
+            handle = op.P._h.value
+        assert op.P._h.value == handle and op.creates == 1
+        Lo, dbo, dgo = adjoint.gradients(h, g, b, ut)
+        assert abs(float(L) - Lo) <= 1e-9 * abs(Lo)
+        assert np.linalg.norm(bt.grad.cpu().numpy() - dbo) <= 1e-8 * np.linalg.norm(dbo)
+        assert np.linalg.norm(gt.grad.cpu().numpy() - dgo) <= 1e-8 * np.linalg.norm(dgo)
+    assert op.setups == 2
+    # a forward with the first field again, then both backwards in reverse
+    # order: each backward solves with its own forward's operator
+    g5, g6 = gaussian_logk(N, s, seed=5, corr=3.0), gaussian_logk(N, s, seed=6, corr=3.0)
+    outs = []
+    for g in (g5, g6):
+        gt = torch.from_numpy(g).to(DEV).requires_grad_(True)
+        u = op(torch.from_numpy(b).to(DEV), gt)
+        outs.append((g, gt, torch.sum((u - torch.from_numpy(ut).to(DEV)) ** 2)))
+    for g, gt, L in reversed(outs):
+        L.backward()
+        _, _, dgo = adjoint.gradients(h, g, b, ut)
+        assert np.linalg.norm(gt.grad.cpu().numpy() - dgo) <= 1e-8 * np.linalg.norm(dgo)
+    assert op.creates == 1
