@@ -278,6 +278,42 @@ amgsym_status amgsym_apply_reduced(amgsym_t h, const void* X_dev, void* Y_dev, i
 amgsym_status amgsym_vcycle(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs,
                             int32_t prec, int32_t finest_hat, void* stream);
 
+/* Per-launch timing of one solve step, for measurement (no counterpart in
+ * the paper: it reports how this library's kernels spend a step of Alg. 1).
+ *
+ * Runs, on `stream`, the launches of one step of amgsym_solve with precision
+ * `prec` (and finest_hat) on b_dev (device FP64 natural order [nrhs][ld]):
+ * the forward transform, the FP64 outer residual, in the mixed modes the
+ * inner reference norm, the PCG start (one V-cycle and z -> p), ONE PCG
+ * iteration (reduced SpMM with <p, q>, the x/r update with <r, r>, the
+ * V-cycle with <r, z>, the p update), in the mixed modes the refinement
+ * update, and the backward transform into x_dev.  A bounded one-thread hold
+ * kernel (about 3 ms of sleeps; it waits on nothing) runs first, so the host
+ * has enqueued the step before the GPU reaches it and the step's kernels run
+ * back to back; each launch is bracketed by two CUDA events on `stream`.
+ * The call synchronises the stream.  No CUDA graph is used.
+ *
+ * out: caller-owned host array of max_records records; record i describes
+ * the i-th timed launch in stream order: the kernel template as a profiler
+ * names it, its role in the step, the V-cycle level (-1 outside it), the
+ * phase (0: once per solve or refinement step, 1: every PCG iteration), the
+ * algorithmic bytes of the launch (matrix storage, X once, Y once, every
+ * epilogue operand once) and the event-timed duration in microseconds.
+ * *count receives the number of timed launches (records beyond max_records
+ * are not written).  Tiny bookkeeping kernels (scalar set-up, zero fills)
+ * run untimed between the records.  Errors as amgsym_solve. */
+typedef struct {
+  char kernel[80];
+  char role[64];
+  int32_t level;
+  int32_t phase;
+  int64_t bytes;
+  double us;
+} amgsym_prof_record;
+amgsym_status amgsym_profile_step(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                                  int32_t prec, int32_t finest_hat, void* stream, amgsym_prof_record* out,
+                                  int32_t max_records, int32_t* count);
+
 /* Failure check of the persistent coarse-cycle kernel (opts->fuse_rows): runs
  * it once on the library's level work arrays with a grid barrier that awaits
  * one arrival more than the grid has, so nothing releases it, and a wait bound

@@ -90,6 +90,17 @@ class SolveInfo(ctypes.Structure):
     ]
 
 
+class ProfRecord(ctypes.Structure):
+    _fields_ = [
+        ("kernel", ctypes.c_char * 80),
+        ("role", ctypes.c_char * 64),
+        ("level", ctypes.c_int32),
+        ("phase", ctypes.c_int32),
+        ("bytes", ctypes.c_int64),
+        ("us", ctypes.c_double),
+    ]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -117,6 +128,7 @@ def _load():
         "amgsym_get_level_matrix": (i32, [P, i32, i32, pi64, pi32, pdbl]),
         "amgsym_level_dia": (i32, [P, i32, i32, pi32, pi32, pi32]),
         "amgsym_cycle_timeout_check": (i32, [P, i32, i32, P]),
+        "amgsym_profile_step": (i32, [P, P, P, i32, i64, i32, i32, P, ctypes.POINTER(ProfRecord), i32, pi32]),
         "amgsym_solve": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
         "amgsym_solve_adjoint": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
         "amgsym_transform_forward": (i32, [P, P, i32, i64, P, P]),
@@ -157,7 +169,7 @@ EXPORTED = [
         "amgsym_apply_reduced amgsym_vcycle amgsym_vcycle_noalloc amgsym_grid_widths amgsym_fv_nnz "
         "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy "
         "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles amgsym_level_dia "
-        "amgsym_cycle_timeout_check"
+        "amgsym_cycle_timeout_check amgsym_profile_step"
     ).split()
 ]
 
@@ -430,6 +442,18 @@ class Problem:
         _check(lib.amgsym_vcycle_noalloc(self._h, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()),
                                          nrhs, prec, 1 if finest_hat else 0, self._stream()))
         return Z
+
+    def profile_step(self, b, x, nrhs: int, prec: int = PREC_MIXED_FP32, finest_hat: bool = False,
+                     max_records: int = 512):
+        """Event-timed launches of one solve step (amgsym_profile_step): a list of
+        dicts with kernel, role, level, phase (1 = every PCG iteration), bytes, us."""
+        recs = (ProfRecord * max_records)()
+        cnt = ctypes.c_int32()
+        _check(lib.amgsym_profile_step(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs,
+                                       self.n, prec, 1 if finest_hat else 0, self._stream(), recs, max_records,
+                                       ctypes.byref(cnt)))
+        return [dict(kernel=r.kernel.decode(), role=r.role.decode(), level=r.level, phase=r.phase, bytes=r.bytes,
+                     us=r.us) for r in recs[: min(cnt.value, max_records)]]
 
     def cycle_timeout_check(self, nrhs: int = 1, prec: int = PREC_MIXED_FP32):
         """Run the persistent coarse-cycle kernel with a barrier nothing releases

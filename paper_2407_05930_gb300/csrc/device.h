@@ -187,6 +187,10 @@ void launch_jacobi(VecType vt, int64_t rows, int32_t C, const void* jd, const vo
                    cudaStream_t st, const int32_t* skip = nullptr);
 void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
                          cudaStream_t st, const int32_t* skip = nullptr);
+// A one-thread kernel that sleeps about naps x 10 us and returns (a bounded
+// loop, it waits on nothing): holds a stream while the host enqueues the
+// launches behind it, so that they then run back to back (per-launch timing).
+void launch_hold(int32_t naps, cudaStream_t st);
 // *dst = v (a one-thread kernel, so the write is ordered on the stream and capturable)
 void launch_set_value(double* dst, double v, cudaStream_t st);
 // CG initial scalars: active = 1 for columns of RHS with nonzero ||b||, status reset.

@@ -467,6 +467,15 @@ void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, c
     coarse_kernel<float><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const float*>(Y), static_cast<float*>(Z), skip);
 }
 
+__global__ void hold_kernel(int32_t naps) {
+  for (int32_t i = 0; i < naps; ++i) __nanosleep(10000);
+}
+
+void launch_hold(int32_t naps, cudaStream_t st) {
+  count_launch();
+  hold_kernel<<<1, 1, 0, st>>>(std::max<int32_t>(0, std::min<int32_t>(naps, 2000)));
+}
+
 __global__ void set_value_kernel(double* dst, double v) { *dst = v; }
 
 void launch_set_value(double* dst, double v, cudaStream_t st) {

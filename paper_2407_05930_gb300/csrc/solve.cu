@@ -34,6 +34,121 @@ void check_launch() {
   if (e != cudaSuccess) fail(AMGSYM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
 }
 
+// ---------------------------------------------------------------------------
+// Per-launch timing hooks (see Profiler in solver.h).
+
+thread_local Profiler* t_prof = nullptr;
+
+ProfScope::ProfScope(cudaStream_t st) : st_(st) {
+  if (!t_prof) return;
+  CK(cudaEventCreate(&ev0_));
+  CK(cudaEventRecord(ev0_, st_));
+}
+
+ProfScope::~ProfScope() {
+  if (ev0_) cudaEventDestroy(ev0_);  // not ended (an error unwound the launch)
+}
+
+void ProfScope::end(const std::string& kernel, const std::string& role, int level, int64_t bytes) {
+  if (!ev0_ || !t_prof) return;
+  ProfRecord r;
+  r.kernel = kernel;
+  r.role = role;
+  r.level = level;
+  r.phase = t_prof->phase;
+  r.bytes = bytes;
+  r.e0 = ev0_;
+  ev0_ = nullptr;
+  CK(cudaEventCreate(&r.e1));
+  CK(cudaEventRecord(r.e1, st_));
+  t_prof->recs.push_back(r);
+}
+
+static const char* tname(ValType t) { return t == VAL_F64 ? "double" : t == VAL_F32 ? "float" : "bf16"; }
+static const char* tname(VecType t) { return t == VEC_F64 ? "double" : "float"; }
+static int64_t vsize(ValType t) { return t == VAL_F64 ? 8 : t == VAL_F32 ? 4 : 2; }
+static int64_t xsize(VecType t) { return t == VEC_F64 ? 8 : 4; }
+
+// Which level matrix M is ("A", "P", "R", "G", "Gt") and its level.
+static std::string matrix_name(const Device* D, const DevCsr& M, int* level) {
+  for (size_t l = 0; l < D->lv.size(); ++l) {
+    const DevLevel& L = D->lv[l];
+    *level = (int)l;
+    if (M.idx == L.A.idx) return "A";
+    if (M.idx == L.P.idx) return "P";
+    if (M.idx == L.R.idx) return "R";
+    if (M.idx == L.G.idx) return "G";
+    if (M.idx == L.Gt.idx) return "Gt";
+  }
+  *level = -1;
+  return "?";
+}
+
+// Algorithmic bytes of one SpMM launch: the matrix (stored diagonals, or CSR
+// values + column indices + row pointers), X once, Y once, each epilogue
+// operand once (an operand that is X itself is not counted twice), the
+// diagonal-smoother vectors and the interface lookups.
+static int64_t spmm_bytes(const Device* D, const DevCsr& M, ValType mt, VecType xt, VecType ot, const SpmmArgs& a) {
+  const int64_t rows = a.rows, C = a.C;
+  int64_t b = 0;
+  if (a.ndiag > 0) {
+    int nstored = 0;
+    for (int d = 0; d < a.ndiag; ++d) nstored = std::max(nstored, a.dsrc[d] + 1);
+    b += (int64_t)nstored * rows * vsize(mt);
+  } else {
+    b += M.nnz * (vsize(mt) + 4) + 4 * (rows + 1);
+  }
+  std::set<const void*> seen;
+  auto rd = [&](const void* p, int64_t n) {
+    if (p && seen.insert(p).second) b += n;
+  };
+  rd(a.X, C * xsize(xt) * (int64_t)M.cols);
+  b += C * xsize(ot) * rows;
+  if (a.beta != 0.0) rd(a.Z, C * xsize(xt) * rows);
+  if (a.dot.mode == DOT_WY) rd(a.dot.W, C * xsize(xt) * rows);
+  if (a.jmode) rd(a.jd, xsize(xt) * rows);
+  if (a.jmode == 1) b += C * xsize(ot) * rows;
+  if (a.imask) {
+    const int64_t words = (rows + 31) / 32;
+    const bool f64 = (mt == VAL_F64) || (xt == VEC_F64);
+    b += words * 8 + ((int64_t)a.nflag + 1) * 4 + (int64_t)a.nflag * 4 +
+         D->iface.n_entries * (4 + (int64_t)a.nb * (f64 ? 8 : 4));
+  }
+  return b;
+}
+
+static void run_spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const SpmmArgs& a) {
+  ProfScope ps(c.st);
+  launch_spmm(mt, xt, ot, a, c.st);
+  check_launch();
+  if (!ps.on()) return;
+  int cpt = 0, kl = 0;
+  spmm_resolved_tile(xt, ot, a, &cpt, &kl);
+  const bool dot = a.dot.mode != DOT_NONE, ifc = a.imask != nullptr, dia = a.ndiag > 0;
+  const std::string kernel = std::string("spmm_kernel<") + tname(mt) + "," + tname(xt) + "," + tname(ot) + "," +
+                             std::to_string(cpt) + "," + std::to_string(kl) + "," + (dot ? "1" : "0") + "," +
+                             (ifc ? "1" : "0") + "," + (dia ? "1" : "0") + ">";
+  int level = -1;
+  std::string role;
+  if (ifc) {
+    role = xt == VEC_F64 && ot == VEC_F32 ? "FP64 outer residual b^ - A^ x^" : "reduced SpMM A^ p";
+    level = -1;
+  } else {
+    const std::string m = matrix_name(c.D, M, &level);
+    role = "L" + std::to_string(level) + " " + m;
+    if (a.jmode == 1)
+      role += " restrict + next-level presmooth";
+    else if (a.jmode == 2)
+      role += " residual + postsmooth";
+    else if (a.beta != 0.0 && a.alpha == -1.0)
+      role += " residual";
+    else if (a.beta != 0.0)
+      role += " update";
+  }
+  if (dot) role += a.dot.mode == DOT_WY ? " + <w,y>" : " + <y,y>";
+  ps.end(kernel, role, level, spmm_bytes(c.D, M, mt, xt, ot, a));
+}
+
 template <typename T>
 static T* dalloc(std::vector<void*>& owner, int64_t count) {
   if (count <= 0) return nullptr;
@@ -378,8 +493,7 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
 void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X, void* Y, double alpha,
           double beta, const void* Z, bool iface, const DotArgs* dot) {
   const SpmmArgs a = make_spmm_args(c, M, mt, xt, ot, X, Y, alpha, beta, Z, iface, dot);
-  launch_spmm(mt, xt, ot, a, c.st);
-  check_launch();
+  run_spmm(c, M, mt, xt, ot, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -469,10 +583,21 @@ void tune_tiles(const Ctx& c) {
 // in one elementwise kernel instead of two products.  `dot` (the fused
 // <r, z> of the final level-0 product) keeps the product form.
 
+static int level_of(const Ctx& c, const DevLevel& L) { return (int)(&L - c.D->lv.data()); }
+
+static void run_jacobi(const Ctx& c, const DevLevel& L, const void* jd, const void* src, void* z, int accumulate) {
+  ProfScope ps(c.st);
+  launch_jacobi(c.vt, L.n, c.C, jd, src, z, accumulate, c.st, c.skip);
+  check_launch();
+  if (ps.on())
+    ps.end(std::string("jacobi_kernel<") + tname(c.vt) + ">",
+           "L" + std::to_string(level_of(c, L)) + (accumulate ? " diagonal smoother z += D r" : " diagonal smoother z = D y"),
+           level_of(c, L), xsize(c.vt) * (int64_t)L.n * (1 + (int64_t)c.C * (accumulate ? 3 : 2)));
+}
+
 static void smooth_first(const Ctx& c, const DevLevel& L, LevelWork& lw, const void* y, void* z) {
   if (const void* jd = L.jd(c.vt)) {
-    launch_jacobi(c.vt, L.n, c.C, jd, y, z, 0, c.st, c.skip);
-    check_launch();
+    run_jacobi(c, L, jd, y, z, 0);
     return;
   }
   spmm(c, L.G, c.mt, c.vt, c.vt, y, lw.t, 1.0, 0.0, nullptr, false, nullptr);
@@ -484,8 +609,7 @@ static void smooth_sweep(const Ctx& c, const DevLevel& L, LevelWork& lw, const v
   spmm(c, L.A, c.mt, c.vt, c.vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
   const void* jd = L.jd(c.vt);
   if (jd && !dot) {
-    launch_jacobi(c.vt, L.n, c.C, jd, lw.r, z, 1, c.st, c.skip);
-    check_launch();
+    run_jacobi(c, L, jd, lw.r, z, 1);
     return;
   }
   spmm(c, L.G, c.mt, c.vt, c.vt, lw.r, lw.t, 1.0, 0.0, nullptr, false, nullptr);
@@ -647,11 +771,21 @@ static const void* vcycle_level(const Ctx& c, std::vector<LevelWork>& lws, int l
   const DevLevel& L = D->lv[l];
   LevelWork& lw = lws[l];
   if (L.cinv) {
-    launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st, c.skip);
-    check_launch();
+    {
+      ProfScope ps(c.st);
+      launch_coarse_solve(c.vt, L.n, c.C, L.cinv, y, z, c.st, c.skip);
+      check_launch();
+      if (ps.on())
+        ps.end(std::string("coarse_kernel<") + tname(c.vt) + ">", "L" + std::to_string(l) + " dense coarsest solve",
+               l, 8 * (int64_t)L.n * L.n + 2 * xsize(c.vt) * (int64_t)L.n * c.C);
+    }
     if (last) {
+      ProfScope ps(c.st);
       launch_dot(c.vt, L.n, c.C, last->W, z, *last, c.st, c.skip);
       check_launch();
+      if (ps.on())
+        ps.end(std::string("dot_kernel<") + tname(c.vt) + ">", "L" + std::to_string(l) + " <w,z>", l,
+               2 * xsize(c.vt) * (int64_t)L.n * c.C);
     }
     return z;
   }
@@ -674,8 +808,7 @@ static const void* vcycle_level(const Ctx& c, std::vector<LevelWork>& lws, int l
       a.jd = Lc.jd(vt);
       a.Y2 = cw.z;
     }
-    launch_spmm(mt, vt, vt, a, c.st);
-    check_launch();
+    run_spmm(c, L.R, mt, vt, vt, a);
   }
   const void* zc = sub(l + 1, cw.y, cw.z, fuse_pre);
   // prolongation and update z += P z_c
@@ -689,8 +822,7 @@ static const void* vcycle_level(const Ctx& c, std::vector<LevelWork>& lws, int l
       SpmmArgs a = make_spmm_args(c, L.A, mt, vt, vt, z, lw.t, -1.0, 1.0, y, hat, nullptr);
       a.jmode = 2;
       a.jd = jd;
-      launch_spmm(mt, vt, vt, a, c.st);
-      check_launch();
+      run_spmm(c, L.A, mt, vt, vt, a);
       return lw.t;
     }
     smooth_sweep(c, L, lw, y, z, hat, fin ? last : nullptr);
@@ -740,12 +872,23 @@ static void pcg_iteration(const Ctx& c, PrecWork& W, const DevScalars& sc, int32
   DotArgs dpq = make_dot(sc, DOT_WY, FIN_ALPHA, W.p, nrhs, D->nb, tol, 0);
   spmm(c, D->Ainn, kmt, c.vt, c.vt, W.p, W.q, 1.0, 0.0, nullptr, true, &dpq);
   DotArgs drr = make_dot(sc, DOT_YY, FIN_CONV, nullptr, nrhs, D->nb, tol, 1);
-  launch_cg_update1(c.vt, D->n_b, c.C, W.x, W.r, W.p, W.q, drr, c.st, c.skip);
-  check_launch();
+  {
+    ProfScope ps(c.st);
+    launch_cg_update1(c.vt, D->n_b, c.C, W.x, W.r, W.p, W.q, drr, c.st, c.skip);
+    check_launch();
+    if (ps.on())
+      ps.end(std::string("cg_update1_kernel<") + tname(c.vt) + ">", "x += a p, r -= a q, <r,r>", -1,
+             6 * xsize(c.vt) * D->n_b * c.C);
+  }
   DotArgs drz = make_dot(sc, DOT_WY, FIN_BETA, W.r, nrhs, D->nb, tol, 0);
   vcycle(c, 0, W.r, W.z, &drz);
-  launch_cg_update2(c.vt, D->n_b, c.C, W.p, W.z, sc.beta, c.st, c.skip);
-  check_launch();
+  {
+    ProfScope ps(c.st);
+    launch_cg_update2(c.vt, D->n_b, c.C, W.p, W.z, sc.beta, c.st, c.skip);
+    check_launch();
+    if (ps.on())
+      ps.end(std::string("cg_update2_kernel<") + tname(c.vt) + ">", "p = z + b p", -1, 3 * xsize(c.vt) * D->n_b * c.C);
+  }
 }
 
 void read_status(Device* D, const DevScalars& sc, cudaStream_t st, int32_t* out4) {
@@ -1111,6 +1254,139 @@ extern "C" amgsym_status amgsym_fv_grad_logk(int32_t d, const int64_t* N, const 
 }
 
 extern "C" int64_t amgsym_kernel_launches(void) { return amgsym::launch_count(); }
+
+// ---------------------------------------------------------------------------
+// Per-launch timing of one solve step (amgsym_profile_step).
+
+namespace {
+
+// Enqueue one step of solve_impl (forward transform, outer residual, PCG
+// start, one PCG iteration, backward transform) with the launch hooks on.
+void profile_step_body(Device* D, amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                       bool mixed, const Ctx& c, cudaStream_t st, Profiler& prof) {
+  const int32_t C = c.C;
+  const VecType vt = c.vt;
+  Ctx c64{D, C, VEC_F64, VAL_F64, false, st};
+  PrecWork& W = mixed ? D->w32 : D->w64;
+  const DevScalars& sc = mixed ? D->sc_in : D->sc_out;
+  const int64_t n = h->n, n_b = D->n_b;
+  auto timed = [&](const std::string& kernel, const std::string& role, int64_t bytes, auto&& launch) {
+    ProfScope ps(st);
+    launch();
+    check_launch();
+    ps.end(kernel, role, -1, bytes);
+  };
+  prof.phase = 0;
+  timed("transform_fwd_kernel<double>", "forward transform b^ = H P b", nrhs * n * 16 + n * 4,
+        [&] { launch_transform_fwd(b_dev, nrhs, ld, D->perm, n_b, D->s, D->bh, VEC_F64, st); });
+  DotArgs dbn = make_dot(D->sc_out, DOT_WY, FIN_STORE_BN, nullptr, nrhs, D->nb, 0.0, 0);
+  timed("dot_kernel<double>", "||b^||^2", 8 * n_b * C, [&] { launch_dot(VEC_F64, n_b, C, D->bh, D->bh, dbn, st); });
+  launch_init_scalars(D->sc_out, nrhs, D->nb, st);
+  launch_set_value(D->sc_out.tol2, 1e-16, st);
+  launch_zero(VEC_F64, n_b * C, D->xh, st);
+  check_launch();
+  DotArgs drr = make_dot(D->sc_out, DOT_YY, FIN_CONV, nullptr, nrhs, D->nb, 0.0, 0);
+  spmm(c64, D->Ainn, VAL_F64, VEC_F64, vt, D->xh, W.r, -1.0, 1.0, D->bh, true, &drr);
+  if (mixed) {
+    launch_set_value(D->sc_in.tol2, 1e-16, st);
+    DotArgs dbi = make_dot(D->sc_in, DOT_WY, FIN_STORE_BN, nullptr, nrhs, D->nb, 0.0, 0);
+    timed("dot_kernel<float>", "||r||^2 (inner reference)", 4 * n_b * C,
+          [&] { launch_dot(VEC_F32, n_b, C, W.r, W.r, dbi, st); });
+    launch_init_scalars(D->sc_in, nrhs, D->nb, st);
+    check_launch();
+    CK(cudaMemcpyAsync(D->sc_in.active, D->sc_out.active, sizeof(int32_t) * C, cudaMemcpyDeviceToDevice, st));
+    launch_zero(VEC_F32, n_b * C, W.x, st);
+    check_launch();
+  }
+  // PCG start: z = M r with <r, z>, p = z
+  DotArgs drz = make_dot(sc, DOT_WY, FIN_STORE_RZ, W.r, nrhs, D->nb, 0.0, 0);
+  vcycle(c, 0, W.r, W.z, &drz);
+  timed(std::string("copy_kernel<") + tname(vt) + ">", "p = z", 2 * xsize(vt) * n_b * C,
+        [&] { launch_copy(vt, n_b * C, W.p, W.z, st); });
+  prof.phase = 1;
+  pcg_iteration(c, W, sc, nrhs, 0.0);
+  prof.phase = 0;
+  if (mixed)
+    timed("add_to_f64_kernel<float>", "x^ += d (refinement update)", n_b * C * (8 + 8 + 4),
+          [&] { launch_add_to_f64(VEC_F32, n_b * C, D->xh, W.x, st); });
+  timed("transform_bwd_kernel<double>", "backward transform x = 2^-s P H x^", nrhs * n * 16 + n * 4,
+        [&] { launch_transform_bwd(D->xh, VEC_F64, nrhs, D->perm, n_b, D->s, x_dev, ld, st); });
+}
+
+}  // namespace
+
+extern "C" amgsym_status amgsym_profile_step(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs,
+                                             int64_t ld, int32_t prec, int32_t finest_hat, void* stream,
+                                             amgsym_prof_record* out, int32_t max_records, int32_t* count) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (nrhs < 1 || (int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
+  if (ld < h->n || !b_dev || !x_dev) fail(AMGSYM_ERR_ARG, "bad vectors or ld");
+  if (!out || !count || max_records < 1) fail(AMGSYM_ERR_ARG, "bad record buffer");
+  if (prec < AMGSYM_PREC_FP64 || prec > AMGSYM_PREC_MIXED_BF16) fail(AMGSYM_ERR_ARG, "unknown precision");
+  const bool mixed = prec != AMGSYM_PREC_FP64;
+  const VecType vt = mixed ? VEC_F32 : VEC_F64;
+  const ValType vmt = prec == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : mixed ? VAL_F32 : VAL_F64;
+  if (mixed && !(h->opts.precisions & (prec == AMGSYM_PREC_MIXED_BF16 ? 4 : 2)))
+    fail(AMGSYM_ERR_STATE, "setup did not build the value precision this mode needs (opts.precisions)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ensure_work(D, nrhs, vt);
+  Ctx c{D, nrhs * D->nb, vt, vmt, finest_hat != 0, st};
+  c.fuse = true;
+  prepare_cycle(c);
+  cudaEvent_t held = nullptr;
+  CK(cudaEventCreateWithFlags(&held, cudaEventDisableTiming));
+  Profiler prof;
+  struct Reset {
+    Profiler* p;
+    cudaEvent_t e;
+    ~Reset() {
+      t_prof = nullptr;
+      for (auto& r : p->recs) {
+        if (r.e0) cudaEventDestroy(r.e0);
+        if (r.e1) cudaEventDestroy(r.e1);
+      }
+      if (e) cudaEventDestroy(e);
+    }
+  } reset{&prof, held};
+  // The hold kernel keeps the stream busy while the host enqueues the step,
+  // so the step's kernels then run back to back and the events between them
+  // time the kernels, not the host.  If the hold ran out before the last
+  // launch was enqueued, try again with a longer one.
+  for (int32_t naps = 300;; naps *= 2) {
+    for (auto& r : prof.recs) {
+      if (r.e0) cudaEventDestroy(r.e0);
+      if (r.e1) cudaEventDestroy(r.e1);
+    }
+    prof.recs.clear();
+    launch_hold(naps, st);
+    check_launch();
+    CK(cudaEventRecord(held, st));
+    t_prof = &prof;
+    profile_step_body(D, h, b_dev, x_dev, nrhs, ld, mixed, c, st, prof);
+    t_prof = nullptr;
+    const cudaError_t q = cudaEventQuery(held);
+    CK(cudaStreamSynchronize(st));
+    if (q == cudaErrorNotReady || naps >= 1600) break;
+    (void)cudaGetLastError();
+  }
+  const int32_t nrec = (int32_t)prof.recs.size();
+  for (int32_t i = 0; i < nrec && i < max_records; ++i) {
+    const ProfRecord& r = prof.recs[i];
+    amgsym_prof_record& o = out[i];
+    std::memset(&o, 0, sizeof(o));
+    std::strncpy(o.kernel, r.kernel.c_str(), sizeof(o.kernel) - 1);
+    std::strncpy(o.role, r.role.c_str(), sizeof(o.role) - 1);
+    o.level = r.level;
+    o.phase = r.phase;
+    o.bytes = r.bytes;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.e0, r.e1));
+    o.us = 1e3 * (double)ms;
+  }
+  *count = nrec;
+  API_END
+}
 
 // ---------------------------------------------------------------------------
 // V-cycle without allocation.

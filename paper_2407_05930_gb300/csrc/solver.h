@@ -127,6 +127,36 @@ struct Ctx {
   bool fuse = false;              // coarse levels as one persistent kernel (Device::fuse_level)
 };
 
+// ---------------------------------------------------------------------------
+// Per-launch timing (amgsym_profile_step): while a Profiler is installed for
+// the calling thread, every instrumented launch is bracketed by two CUDA
+// events on its stream and recorded with its kernel, its role in the solve
+// and its algorithmic bytes.  Without one the hooks cost a thread-local load.
+struct ProfRecord {
+  std::string kernel, role;
+  int32_t level = -1, phase = 0;
+  int64_t bytes = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+struct Profiler {
+  std::vector<ProfRecord> recs;
+  int32_t phase = 0;  // 0: once per solve / refinement step, 1: every PCG iteration
+};
+extern thread_local Profiler* t_prof;
+class ProfScope {
+ public:
+  explicit ProfScope(cudaStream_t st);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+  bool on() const { return ev0_ != nullptr; }
+  void end(const std::string& kernel, const std::string& role, int level, int64_t bytes);
+
+ private:
+  cudaStream_t st_;
+  cudaEvent_t ev0_ = nullptr;
+};
+
 // Build (outside graph capture) the persistent coarse-cycle plan the V-cycle
 // of this context will use, and check the barrier error word after a run.
 void prepare_cycle(const Ctx& c);
