@@ -115,6 +115,18 @@ typedef struct {
                                fsai_max_lower); 1 = diagonal, i.e. damped Jacobi with the
                                same omega rule.  Default 1: at 256^3 it gave 80 inner
                                iterations at 0.91 ms against 78 at 0.97 ms with 4 */
+  int32_t halo_kb;          /* halo-staged products: the CSR matrices below the finest level
+                               (A_l for l >= 1, P_l, R_l) are also cut into tiles of
+                               consecutive rows, each with the sorted list of the X rows it
+                               reads (its halo) and 16-bit column indices into that list;
+                               a product stages a tile's halo in shared memory once and
+                               gathers from there instead of through L1.  The tile height is
+                               the largest of 256, 128, 64, 32 rows whose largest halo takes
+                               at most halo_kb KiB at 8 FP32 columns; a launch whose halo
+                               would exceed 100 KiB of shared memory (many columns, FP64)
+                               runs the CSR kernel.  Same entry and lane order as the CSR
+                               kernel, so results are bit-identical.  0 = CSR only;
+                               default 64 */
 } amgsym_opts;
 
 #define AMGSYM_MAX_DIAG 8

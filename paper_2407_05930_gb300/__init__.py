@@ -64,6 +64,7 @@ class Opts(ctypes.Structure):
         ("dia_max_diag", ctypes.c_int32),
         ("fuse_rows", ctypes.c_int32),
         ("fsai_max_lower_coarse", ctypes.c_int32),
+        ("halo_kb", ctypes.c_int32),
     ]
 
 

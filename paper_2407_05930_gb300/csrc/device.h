@@ -42,6 +42,15 @@ struct DevCsr {
   const void* dvals(ValType t) const {
     return t == VAL_F64 ? (const void*)dv64 : t == VAL_F32 ? (const void*)dv32 : (const void*)dv16;
   }
+  // Halo-staged form (htiles > 0): tiles of hrows consecutive rows; tile t
+  // reads the X rows hx[hptr[t] .. hptr[t+1]) (sorted, hmax at most, hsum in
+  // all), and entry k's column is hx[hptr[t] + lidx[k]].  Values and row
+  // pointers are the CSR arrays above.
+  int32_t htiles = 0, hrows = 0, hmax = 0;
+  int64_t hsum = 0;
+  int32_t* hptr = nullptr;
+  int32_t* hx = nullptr;
+  uint16_t* lidx = nullptr;
 };
 
 // Interface couplings A_out,i of eq. "hL_splitting" in a form the SpMM can
@@ -154,6 +163,13 @@ struct SpmmArgs {
   int32_t jmode = 0;
   const void* jd = nullptr;
   void* Y2 = nullptr;
+  // Halo-staged form of a CSR matrix (htiles > 0; see DevCsr): used by
+  // launch_spmm for products without a dot or interface when the largest halo
+  // fits the shared-memory limit, else the CSR kernel runs.
+  int32_t htiles = 0, hrows = 0, hmax = 0;
+  const int32_t* hptr = nullptr;
+  const int32_t* hx = nullptr;
+  const uint16_t* lidx = nullptr;
   DotArgs dot;
 };
 
@@ -161,6 +177,8 @@ struct SpmmArgs {
 void launch_spmm(ValType mt, VecType xt, VecType ot, const SpmmArgs& a, cudaStream_t st);
 // The (columns per thread, entry lanes) launch_spmm runs for these arguments.
 void spmm_resolved_tile(VecType xt, VecType ot, const SpmmArgs& a, int* cpt, int* kl);
+// Whether launch_spmm runs the halo-staged kernel for these arguments.
+bool spmm_uses_halo(VecType xt, const SpmmArgs& a);
 
 // Elementwise / transform / small kernels (k_misc.cu).
 void launch_transform_fwd(const double* b, int32_t nrhs, int64_t ld, const int32_t* perm, int64_t n_b,

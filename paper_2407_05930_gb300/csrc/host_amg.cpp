@@ -690,7 +690,8 @@ extern "C" amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts) {
   amgsym_opts_default(&o);
   if (opts) o = *opts;
   if (o.nu < 1 || o.nu > 8) fail(AMGSYM_ERR_ARG, "nu must be in [1, 8]");
-  if (o.fuse_rows < 0 || o.dia_max_diag < 0) fail(AMGSYM_ERR_ARG, "fuse_rows and dia_max_diag must be >= 0");
+  if (o.fuse_rows < 0 || o.dia_max_diag < 0 || o.halo_kb < 0)
+    fail(AMGSYM_ERR_ARG, "fuse_rows, dia_max_diag and halo_kb must be >= 0");
   if (o.fsai_max_lower < 1 || o.fsai_max_lower > 32 || o.fsai_max_lower_coarse < 1 || o.fsai_max_lower_coarse > 32)
     fail(AMGSYM_ERR_ARG, "fsai_max_lower and fsai_max_lower_coarse must be in [1, 32]");
   if (o.coarse_max < 1 || o.coarse_max > kDenseLimit) fail(AMGSYM_ERR_ARG, "coarse_max out of range");

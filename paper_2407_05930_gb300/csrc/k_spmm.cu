@@ -28,6 +28,8 @@
 // an optional per-column dot (W.Y or Y.Y) reduced deterministically.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "spmm_common.cuh"
 
 namespace amgsym {
@@ -52,6 +54,109 @@ __global__ void __launch_bounds__(kBlock, ((DIA || CPT >= 8) ? 4 : (HAS_DOT || H
     block_dot<CPT>(a.dot, part, t.c0, t.slot_ok && t.e == 0, t.g, t.rows_pb, t.S, a.C, sm, blockIdx.x,
                    gridDim.x, a.dot.sc.partials, a.dot.sc.ticket);
   }
+}
+
+// Halo-staged CSR product (the CSR matrices below the finest level).  The
+// gathers of a coarse-level product are scattered: a warp's 32 lanes fetch
+// 32-byte X rows from up to 32 different lines, and the product is bound by
+// the L1 tag stage, not by DRAM.  Here the rows are cut into tiles; a block
+// first copies the tile's halo -- the sorted list of X rows the tile reads --
+// into shared memory with coalesced 16-byte loads (each halo row once per
+// tile), then computes the tile's rows from shared memory with 16-bit local
+// column indices.  The entry lanes, batches and fma order are those of the
+// CSR kernel (halo_row / csr_row), so the products are bit-identical.
+// Tiles are walked grid-stride by a full wave of resident blocks.
+constexpr int kHaloSmemLimit = 100 * 1024;
+
+template <typename MT, typename XT, typename OT, int CPT, int KL>
+__global__ void __launch_bounds__(kBlock) spmm_halo_kernel(SpmmArgs a) {
+  if (a.skip && *a.skip == 0) return;  // uniform over the grid
+  using CT = typename ComputeOf<MT, XT>::type;
+  using DT = typename AccOf<XT>::type;
+  extern __shared__ __align__(16) unsigned char halo_smem[];
+  XT* xs = reinterpret_cast<XT*>(halo_smem);
+  const int C = a.C;
+  const int TPC = C / CPT;
+  const int S = TPC * KL;
+  const int rows_pb = kBlock / S;
+  const int g = threadIdx.x / S;
+  const int w = threadIdx.x - g * S;
+  const int e = KL > 1 ? w / TPC : 0;
+  const int c0 = (w - e * TPC) * CPT;
+  const bool slot_ok = g < rows_pb;
+  const int words = C * (int)sizeof(XT) / 4;  // 32-bit words per X row
+  const uint32_t* __restrict__ Xw = static_cast<const uint32_t*>(a.X);
+  uint32_t* xsw = reinterpret_cast<uint32_t*>(halo_smem);
+  const int32_t* __restrict__ ptr = a.ptr;
+  DT dpart[CPT];
+  for (int t = blockIdx.x; t < a.htiles; t += gridDim.x) {
+    const int h0 = __ldg(a.hptr + t), nh = __ldg(a.hptr + t + 1) - h0;
+    if ((words & 3) == 0) {
+      const int q = words >> 2;  // 16-byte vectors per X row
+      const uint4* __restrict__ X4 = reinterpret_cast<const uint4*>(Xw);
+      uint4* xs4 = reinterpret_cast<uint4*>(xsw);
+      for (int j = threadIdx.x; j < nh * q; j += kBlock) {
+        const int h = j / q, v = j - h * q;
+        xs4[j] = __ldg(X4 + (int64_t)__ldg(a.hx + h0 + h) * q + v);
+      }
+    } else {
+      for (int j = threadIdx.x; j < nh * words; j += kBlock) {
+        const int h = j / words, v = j - h * words;
+        xsw[j] = __ldg(Xw + (int64_t)__ldg(a.hx + h0 + h) * words + v);
+      }
+    }
+    __syncthreads();
+    const int r1 = min(t * a.hrows + a.hrows, a.rows);
+    for (int base = t * a.hrows; base < r1; base += rows_pb) {
+      const int row = base + g;
+      const bool live = slot_ok && row < r1;
+      CT acc[CPT];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
+      if (live) halo_row<MT, XT, CT, CPT, KL>(a, xs, __ldg(ptr + row), __ldg(ptr + row + 1), e, c0, acc);
+      if (KL > 1) {
+#pragma unroll
+        for (int off = KL / 2; off >= 1; off >>= 1) {
+#pragma unroll
+          for (int q = 0; q < CPT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off * TPC);
+        }
+      }
+      if (live && e == 0) row_epilogue<XT, OT, CT, DT, CPT, false, false>(a, row, c0, acc, nullptr, dpart);
+    }
+    __syncthreads();  // the next tile overwrites the halo
+  }
+}
+
+static size_t halo_smem_bytes(VecType xt, const SpmmArgs& a) {
+  return (size_t)a.hmax * (size_t)a.C * (xt == VEC_F64 ? 8 : 4);
+}
+
+bool spmm_uses_halo(VecType xt, const SpmmArgs& a) {
+  return a.htiles > 0 && a.hptr && a.ndiag <= 0 && a.dot.mode == DOT_NONE && !a.imask &&
+         halo_smem_bytes(xt, a) <= (size_t)kHaloSmemLimit;
+}
+
+template <typename MT, typename XT, typename OT, int CPT, int KL>
+static void launch_h(const SpmmArgs& a, cudaStream_t st) {
+  auto kern = spmm_halo_kernel<MT, XT, OT, CPT, KL>;
+  const size_t smem = (size_t)a.hmax * (size_t)a.C * sizeof(XT);
+  if (smem > 48 * 1024) {
+    // above 48 KiB a kernel must opt in, once per device (per instantiation)
+    static std::mutex mu;
+    static uint64_t devices_set = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) fail(AMGSYM_ERR_CUDA, "no current device");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!(devices_set >> dev & 1)) {
+      if (cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemLimit) !=
+          cudaSuccess)
+        fail(AMGSYM_ERR_CUDA, "cannot raise the shared memory of the halo-staged SpMM");
+      devices_set |= uint64_t(1) << dev;
+    }
+  }
+  count_launch();
+  const int g = std::max(1, std::min(a.htiles, resident_grid((const void*)kern, smem)));
+  kern<<<g, kBlock, smem, st>>>(a);
 }
 
 template <typename MT, typename XT, typename OT, int CPT, int KL, bool DIA = false>
@@ -95,6 +200,16 @@ static void launch_t(const SpmmArgs& a, cudaStream_t st) {
   int kl = a.kl > 0 ? a.kl : 1;
   if (TPC & (TPC - 1)) kl = 1;
   while (kl > 1 && TPC * kl > 32) kl >>= 1;
+  if (spmm_uses_halo(sizeof(XT) == 8 ? VEC_F64 : VEC_F32, a)) {
+    switch (kl) {
+      case 1: launch_h<MT, XT, OT, CPT, 1>(a, st); break;
+      case 2: launch_h<MT, XT, OT, CPT, 2>(a, st); break;
+      case 4: launch_h<MT, XT, OT, CPT, 4>(a, st); break;
+      case 8: launch_h<MT, XT, OT, CPT, 8>(a, st); break;
+      default: launch_h<MT, XT, OT, CPT, 16>(a, st); break;
+    }
+    return;
+  }
   switch (kl) {
     case 1: launch_k<MT, XT, OT, CPT, 1>(a, st); break;
     case 2: launch_k<MT, XT, OT, CPT, 2>(a, st); break;

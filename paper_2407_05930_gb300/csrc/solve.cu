@@ -95,6 +95,9 @@ static int64_t spmm_bytes(const Device* D, const DevCsr& M, ValType mt, VecType 
     int nstored = 0;
     for (int d = 0; d < a.ndiag; ++d) nstored = std::max(nstored, a.dsrc[d] + 1);
     b += (int64_t)nstored * rows * vsize(mt);
+  } else if (spmm_uses_halo(xt, a)) {
+    // values, 16-bit local columns, row pointers, tile halo pointers and lists
+    b += M.nnz * (vsize(mt) + 2) + 4 * (rows + 1) + 4 * ((int64_t)M.htiles + 1) + 4 * M.hsum;
   } else {
     b += M.nnz * (vsize(mt) + 4) + 4 * (rows + 1);
   }
@@ -125,7 +128,7 @@ static void run_spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecT
   int cpt = 0, kl = 0;
   spmm_resolved_tile(xt, ot, a, &cpt, &kl);
   const bool dot = a.dot.mode != DOT_NONE, ifc = a.imask != nullptr, dia = a.ndiag > 0;
-  const std::string kernel = std::string("spmm_kernel<") + tname(mt) + "," + tname(xt) + "," + tname(ot) + "," +
+  const std::string kernel = std::string(spmm_uses_halo(xt, a) ? "spmm_halo_kernel<" : "spmm_kernel<") + tname(mt) + "," + tname(xt) + "," + tname(ot) + "," +
                              std::to_string(cpt) + "," + std::to_string(kl) + "," + (dot ? "1" : "0") + "," +
                              (ifc ? "1" : "0") + "," + (dia ? "1" : "0") + ">";
   int level = -1;
@@ -165,7 +168,55 @@ static T* upload(std::vector<void*>& owner, const T* src, int64_t count) {
   return d;
 }
 
-static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions, const Dia* dia = nullptr) {
+// Halo tiles of a CSR matrix (the halo-staged product, see DevCsr): the
+// largest tile height of 256, 128, 64 or 32 rows whose largest halo (distinct
+// columns of a tile) takes at most budget_bytes at 32 bytes per X row (8 FP32
+// columns) and fits 16-bit local indices.  False if none does.
+struct HostHalo {
+  int32_t rows = 0, hmax = 0;
+  std::vector<int32_t> hptr, hx;
+  std::vector<uint16_t> lidx;
+};
+
+static bool build_halo(const Csr& M, int64_t budget_bytes, HostHalo& H) {
+  const int64_t n = M.rows;
+  if (n <= 0 || M.nnz() == 0 || budget_bytes <= 0) return false;
+  for (int R : {256, 128, 64, 32}) {
+    const int64_t nt = (n + R - 1) / R;
+    std::vector<int32_t> size((size_t)nt);
+    int32_t hmax = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(max : hmax)
+    for (int64_t t = 0; t < nt; ++t) {
+      const int64_t kb = M.ptr[t * R], ke = M.ptr[std::min(n, (t + 1) * R)];
+      std::vector<int32_t> c(M.idx.begin() + kb, M.idx.begin() + ke);
+      std::sort(c.begin(), c.end());
+      size[t] = (int32_t)(std::unique(c.begin(), c.end()) - c.begin());
+      hmax = std::max(hmax, size[t]);
+    }
+    if ((int64_t)hmax * 32 > budget_bytes || hmax > 65535) continue;
+    H.rows = R;
+    H.hmax = hmax;
+    H.hptr.assign((size_t)nt + 1, 0);
+    for (int64_t t = 0; t < nt; ++t) H.hptr[t + 1] = H.hptr[t] + size[t];
+    H.hx.resize((size_t)H.hptr[nt]);
+    H.lidx.resize((size_t)M.nnz());
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < nt; ++t) {
+      const int64_t kb = M.ptr[t * R], ke = M.ptr[std::min(n, (t + 1) * R)];
+      int32_t* h = H.hx.data() + H.hptr[t];
+      std::vector<int32_t> c(M.idx.begin() + kb, M.idx.begin() + ke);
+      std::sort(c.begin(), c.end());
+      std::copy(c.begin(), std::unique(c.begin(), c.end()), h);
+      for (int64_t k = kb; k < ke; ++k)
+        H.lidx[k] = (uint16_t)(std::lower_bound(h, h + size[t], M.idx[k]) - h);
+    }
+    return true;
+  }
+  return false;
+}
+
+static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions, const Dia* dia = nullptr,
+                         int halo_kb = 0) {
   DevCsr D;
   if (M.rows > INT32_MAX || M.nnz() > INT32_MAX) fail(AMGSYM_ERR_ARG, "matrix too large for 32-bit device indices");
   D.rows = (int32_t)M.rows;
@@ -212,6 +263,16 @@ static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions
       for (int64_t i = 0; i < cnt; ++i) v[i] = __float2bfloat16((float)padded[i]);
       D.dv16 = upload(owner, v.data(), cnt);
     }
+  }
+  HostHalo H;
+  if (D.ndiag == 0 && halo_kb > 0 && build_halo(M, (int64_t)halo_kb * 1024, H)) {
+    D.htiles = (int32_t)(H.hptr.size() - 1);
+    D.hrows = H.rows;
+    D.hmax = H.hmax;
+    D.hsum = H.hptr.back();
+    D.hptr = upload(owner, H.hptr.data(), (int64_t)H.hptr.size());
+    D.hx = upload(owner, H.hx.data(), (int64_t)H.hx.size());
+    D.lidx = upload(owner, H.lidx.data(), (int64_t)H.lidx.size());
   }
   return D;
 }
@@ -266,14 +327,15 @@ void device_upload(amgsym_problem* p) {
     V.n = (int32_t)L.A.rows;
     V.omega = L.omega;
     // level 0 keeps FP64 always (the reduced operator of the outer loop)
-    V.A = upload_csr(D->owned, L.A, l == 0 ? D->precisions : p->opts.precisions, &L.Adia);
+    const int hkb = p->opts.halo_kb;
+    V.A = upload_csr(D->owned, L.A, l == 0 ? D->precisions : p->opts.precisions, &L.Adia, hkb);
     if (!L.coarse_inv.empty()) {
       V.cinv = upload(D->owned, L.coarse_inv.data(), (int64_t)L.coarse_inv.size());
     } else {
-      V.P = upload_csr(D->owned, L.P, p->opts.precisions);
-      V.R = upload_csr(D->owned, L.R, p->opts.precisions);
-      V.G = upload_csr(D->owned, L.G, p->opts.precisions, &L.Gdia);
-      V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions, &L.Gtdia);
+      V.P = upload_csr(D->owned, L.P, p->opts.precisions, nullptr, hkb);
+      V.R = upload_csr(D->owned, L.R, p->opts.precisions, nullptr, hkb);
+      V.G = upload_csr(D->owned, L.G, p->opts.precisions, &L.Gdia, hkb);
+      V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions, &L.Gtdia, hkb);
       // a diagonal FSAI factor: the smoother is the diagonal omega g_ii^2
       bool diag = L.G.nnz() == L.G.rows;
       for (int64_t i = 0; diag && i < L.G.rows; ++i) diag = L.G.idx[L.G.ptr[i]] == (int32_t)i;
@@ -475,6 +537,14 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
     }
     a.dval = M.dvals(mt);
     a.dstride = M.dstride;
+  }
+  if (M.htiles > 0 && a.ndiag == 0) {
+    a.htiles = M.htiles;
+    a.hrows = M.hrows;
+    a.hmax = M.hmax;
+    a.hptr = M.hptr;
+    a.hx = M.hx;
+    a.lidx = M.lidx;
   }
   if (dot) a.dot = *dot;
   a.skip = c.skip;

@@ -198,6 +198,44 @@ __device__ __forceinline__ void csr_row(const SpmmArgs& a, int kb, int ke, int e
   }
 }
 
+// The entries kb + e, kb + e + KL, ... < ke of one row of a halo-staged
+// matrix: the same batches, masking and fma sequence as csr_row (so the same
+// sums), with 16-bit column indices into the tile's halo and the gathered
+// rows read from shared memory (xs: [halo][C], staged by the caller).
+template <typename MT, typename XT, typename CT, int CPT, int KL>
+__device__ __forceinline__ void halo_row(const SpmmArgs& a, const XT* xs, int kb, int ke, int e, int c0,
+                                         CT (&acc)[CPT]) {
+  const MT* __restrict__ val = static_cast<const MT*>(a.val);
+  const uint16_t* __restrict__ li = a.lidx;
+  const int C = a.C;
+  constexpr int U = CPT >= 8 ? 2 : 4;
+  for (int k = kb + e; k < ke; k += U * KL) {
+    int j[U];
+    CT m[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = k + u * KL < ke;
+      j[u] = ok ? (int)__ldg(li + k + u * KL) : 0;
+      m[u] = ok ? cvt<CT>(val[k + u * KL]) : (CT)0;
+    }
+    Vec<XT, CPT> x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (k + u * KL < ke) {
+        x[u] = *reinterpret_cast<const Vec<XT, CPT>*>(xs + j[u] * C + c0);
+      } else {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) x[u].v[q] = (XT)0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) acc[q] = fma(m[u], (CT)x[u].v[q], acc[q]);
+    }
+  }
+}
+
 // The interface couplings of flagged row number f (A_out,i of eq.
 // "hL_splitting"; one value per block column).
 template <typename XT, typename CT, int CPT, bool COH>
