@@ -125,8 +125,8 @@ typedef struct {
                                at most halo_kb KiB at 8 FP32 columns; a launch whose halo
                                would exceed 100 KiB of shared memory (many columns, FP64)
                                runs the CSR kernel.  Same entry and lane order as the CSR
-                               kernel, so results are bit-identical.  0 = CSR only;
-                               default 64 */
+                               kernel, so results are bit-identical.  0 = CSR only
+                               (default) */
 } amgsym_opts;
 
 #define AMGSYM_MAX_DIAG 8

@@ -18,6 +18,11 @@ it stays symmetric on stretched grids:
 
 Unknowns are in natural lexicographic order with x fastest.  The right-hand
 side of a source density ``f`` is ``f`` times the cell volume.
+
+``bc="neumann"`` gives the paper's model problem (Sec. 2.2, eq.
+"modelproblem": homogeneous Neumann on every wall): the boundary faces carry
+no flux, so their transmissibility drops out of the diagonal, every row sums
+to zero and the constant vector spans the null space.
 """
 
 from __future__ import annotations
@@ -86,8 +91,17 @@ def transmissibilities(h, k: np.ndarray):
     return out
 
 
-def assemble(h, k: np.ndarray) -> sp.csr_matrix:
+def _boundary_weight(bc: str) -> float:
+    if bc == "dirichlet":
+        return 1.0
+    if bc == "neumann":
+        return 0.0
+    raise ValueError(f"unknown boundary condition {bc!r}")
+
+
+def assemble(h, k: np.ndarray, bc: str = "dirichlet") -> sp.csr_matrix:
     """Full unreduced operator ``A`` (CSR, FP64, natural order, x fastest)."""
+    wb = _boundary_weight(bc)
     d = len(h)
     N = [x.size for x in h]
     n = int(np.prod(N))
@@ -117,8 +131,8 @@ def assemble(h, k: np.ndarray) -> sp.csr_matrix:
         last = [slice(None)] * d
         first[ax] = slice(0, 1)
         last[ax] = slice(N[a] - 1, N[a])
-        s_low[tuple(first)] = t_low
-        s_high[tuple(last)] = t_high
+        s_low[tuple(first)] = wb * t_low
+        s_high[tuple(last)] = wb * t_high
         diag = diag + (s_low + s_high)
     allr = np.arange(n)
     rows.append(allr)
@@ -130,9 +144,10 @@ def assemble(h, k: np.ndarray) -> sp.csr_matrix:
     return A
 
 
-def apply(h, k: np.ndarray, u: np.ndarray) -> np.ndarray:
+def apply(h, k: np.ndarray, u: np.ndarray, bc: str = "dirichlet") -> np.ndarray:
     """Matrix-free ``A u`` from the face fluxes ``t_f (u_p - u_q)``; used for
     residual checks at sizes where assembling ``A`` is wasteful."""
+    wb = _boundary_weight(bc)
     d = len(h)
     N = [x.size for x in h]
     U = np.asarray(u, dtype=np.float64).reshape(N[::-1])
@@ -152,16 +167,16 @@ def apply(h, k: np.ndarray, u: np.ndarray) -> np.ndarray:
         last = [slice(None)] * d
         first[ax] = slice(0, 1)
         last[ax] = slice(N[a] - 1, N[a])
-        out[tuple(first)] += t_low * U[tuple(first)]
-        out[tuple(last)] += t_high * U[tuple(last)]
+        out[tuple(first)] += wb * t_low * U[tuple(first)]
+        out[tuple(last)] += wb * t_high * U[tuple(last)]
     return out.reshape(-1)
 
 
-def grid_operator(N, gamma: float, logk: np.ndarray | None = None):
+def grid_operator(N, gamma: float, logk: np.ndarray | None = None, bc: str = "dirichlet"):
     """Convenience: widths, k and assembled ``A`` for a unit-cube grid."""
     from .grid import widths
 
     h = widths(N, gamma)
     n = int(np.prod(N))
     k = np.ones(n) if logk is None else np.exp(logk)
-    return h, k, assemble(h, k)
+    return h, k, assemble(h, k, bc)

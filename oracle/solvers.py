@@ -121,13 +121,16 @@ def _axis_weights(N):
     return c
 
 
-def closed_form_eigenvalues(N) -> np.ndarray:
-    """Sorted spectrum of the uniform unit-coefficient Dirichlet operator."""
+def closed_form_eigenvalues(N, bc: str = "dirichlet") -> np.ndarray:
+    """Sorted spectrum of the uniform unit-coefficient operator.  Dirichlet:
+    modes m = 1..N per axis; Neumann: the 1D operator is tridiag(-1, 2, -1)
+    with corner entries 1, eigenpairs 4 sin^2(m pi / (2N)) and
+    cos(m pi (j + 1/2) / N), m = 0..N-1 (m = 0 the constant, eigenvalue 0)."""
     N = tuple(int(v) for v in N)
     c = _axis_weights(N)
     lam = np.zeros([1] * len(N))
     for a, n in enumerate(N):
-        m = np.arange(1, n + 1, dtype=np.float64)
+        m = np.arange(1, n + 1, dtype=np.float64) if bc == "dirichlet" else np.arange(n, dtype=np.float64)
         l1 = c[a] * 4.0 * np.sin(m * np.pi / (2.0 * n)) ** 2
         shape = [1] * len(N)
         shape[a] = n
@@ -172,3 +175,57 @@ def dst_solve(N, b: np.ndarray) -> np.ndarray:
         out[r] = U
     out = out.reshape(B.shape[0], -1)
     return out[0] if single else out
+
+
+def _cosine_basis(n: int) -> np.ndarray:
+    """Orthonormal DCT-II basis ``C[m, j] = c_m cos(m pi (j + 1/2) / n)``,
+    ``m = 0..n-1``: the eigenvectors of the 1D Neumann operator."""
+    m = np.arange(n, dtype=np.float64)[:, None]
+    j = np.arange(n, dtype=np.float64)[None, :]
+    Cb = np.cos(m * np.pi * (j + 0.5) / n) * np.sqrt(2.0 / n)
+    Cb[0] = np.sqrt(1.0 / n)
+    return Cb
+
+
+def neumann_dct_solve(N, b: np.ndarray) -> np.ndarray:
+    """Minimum-norm solution of the uniform unit-coefficient Neumann problem
+    (the paper's model problem, Sec. 2.2, on a uniform grid): transform ``b``
+    to the separable cosine basis, divide by the eigenvalues, drop the
+    constant mode (eigenvalue 0; a compatible ``b`` has none), transform back.
+    The result has zero mean.  ``b``: one vector or a stack ``(nrhs, n)``."""
+    N = tuple(int(v) for v in N)
+    d = len(N)
+    c = _axis_weights(N)
+    b = np.asarray(b, dtype=np.float64)
+    single = b.ndim == 1
+    B = b.reshape((-1,) + N[::-1])
+    lam = np.zeros([1] * d)
+    for a, n in enumerate(N):
+        m = np.arange(n, dtype=np.float64)
+        shape = [1] * d
+        shape[d - 1 - a] = n
+        lam = lam + (c[a] * 4.0 * np.sin(m * np.pi / (2.0 * n)) ** 2).reshape(shape)
+    inv = np.zeros_like(lam)
+    nz = lam > 0.0
+    inv[nz] = 1.0 / lam[nz]
+    out = np.empty_like(B)
+    for r in range(B.shape[0]):
+        U = B[r]
+        for a, n in enumerate(N):
+            U = np.moveaxis(np.tensordot(_cosine_basis(n), U, axes=([1], [d - 1 - a])), 0, d - 1 - a)
+        U = U * inv
+        for a, n in enumerate(N):
+            U = np.moveaxis(np.tensordot(_cosine_basis(n).T, U, axes=([1], [d - 1 - a])), 0, d - 1 - a)
+        out[r] = U
+    out = out.reshape(B.shape[0], -1)
+    return out[0] if single else out
+
+
+def min_norm_solve(A, b: np.ndarray) -> np.ndarray:
+    """Minimum-norm solution of a singular consistent symmetric system by the
+    dense eigendecomposition (eigenvalues below 1e-12 of the largest treated
+    as zero): the reference for the Neumann problem at small ``n``."""
+    Ad = A.toarray() if sp.issparse(A) else np.asarray(A)
+    w, V = np.linalg.eigh(Ad)
+    keep = w > 1e-12 * w[-1]
+    return V[:, keep] @ ((V[:, keep].T @ b) / w[keep][:, None] if np.ndim(b) == 2 else (V[:, keep].T @ b) / w[keep])

@@ -62,7 +62,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->dia_max_diag = AMGSYM_MAX_DIAG;
   o->fuse_rows = 0;
   o->fsai_max_lower_coarse = 1;
-  o->halo_kb = 64;
+  o->halo_kb = 0;
 }
 
 extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {

@@ -69,10 +69,12 @@ __global__ void __launch_bounds__(kBlock, ((DIA || CPT >= 8) ? 4 : (HAS_DOT || H
 constexpr int kHaloSmemLimit = 100 * 1024;
 
 template <typename MT, typename XT, typename OT, int CPT, int KL>
-__global__ void __launch_bounds__(kBlock) spmm_halo_kernel(SpmmArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) spmm_halo_kernel(SpmmArgs a) {
   if (a.skip && *a.skip == 0) return;  // uniform over the grid
   using CT = typename ComputeOf<MT, XT>::type;
   using DT = typename AccOf<XT>::type;
+  constexpr int CH = 4;    // staging loads in flight per thread
+  constexpr int MAXP = 2;  // passes of a tile whose row pointers load before the staging
   extern __shared__ __align__(16) unsigned char halo_smem[];
   XT* xs = reinterpret_cast<XT*>(halo_smem);
   const int C = a.C;
@@ -85,43 +87,103 @@ __global__ void __launch_bounds__(kBlock) spmm_halo_kernel(SpmmArgs a) {
   const int c0 = (w - e * TPC) * CPT;
   const bool slot_ok = g < rows_pb;
   const int words = C * (int)sizeof(XT) / 4;  // 32-bit words per X row
-  const uint32_t* __restrict__ Xw = static_cast<const uint32_t*>(a.X);
-  uint32_t* xsw = reinterpret_cast<uint32_t*>(halo_smem);
+  const bool vec16 = (words & 3) == 0;
+  const int q = vec16 ? words >> 2 : words;   // staged units per X row (16 or 4 bytes)
   const int32_t* __restrict__ ptr = a.ptr;
   DT dpart[CPT];
-  for (int t = blockIdx.x; t < a.htiles; t += gridDim.x) {
-    const int h0 = __ldg(a.hptr + t), nh = __ldg(a.hptr + t + 1) - h0;
-    if ((words & 3) == 0) {
-      const int q = words >> 2;  // 16-byte vectors per X row
-      const uint4* __restrict__ X4 = reinterpret_cast<const uint4*>(Xw);
-      uint4* xs4 = reinterpret_cast<uint4*>(xsw);
-      for (int j = threadIdx.x; j < nh * q; j += kBlock) {
-        const int h = j / q, v = j - h * q;
-        xs4[j] = __ldg(X4 + (int64_t)__ldg(a.hx + h0 + h) * q + v);
+  int t = blockIdx.x;
+  int hb_next = 0, he_next = 0;
+  if (t < a.htiles) {
+    hb_next = __ldg(a.hptr + t);
+    he_next = __ldg(a.hptr + t + 1);
+  }
+  for (; t < a.htiles; t += gridDim.x) {
+    const int h0 = hb_next, nh = he_next - hb_next;
+    const int r0 = t * a.hrows, r1 = min(r0 + a.hrows, a.rows);
+    // independent of the halo: this thread's row pointers of the first
+    // passes, issued before the staging loads
+    int kb[MAXP], ke[MAXP];
+#pragma unroll
+    for (int p = 0; p < MAXP; ++p) {
+      const int row = r0 + p * rows_pb + g;
+      kb[p] = ke[p] = 0;
+      if (slot_ok && row < r1) {
+        kb[p] = __ldg(ptr + row);
+        ke[p] = __ldg(ptr + row + 1);
       }
-    } else {
-      for (int j = threadIdx.x; j < nh * words; j += kBlock) {
-        const int h = j / words, v = j - h * words;
-        xsw[j] = __ldg(Xw + (int64_t)__ldg(a.hx + h0 + h) * words + v);
+    }
+    const int tn = t + gridDim.x;
+    if (tn < a.htiles) {
+      hb_next = __ldg(a.hptr + tn);
+      he_next = __ldg(a.hptr + tn + 1);
+    }
+    // stage the halo: CH units per thread per round, every index load of the
+    // round first, then every X load, then the shared-memory stores
+    const int total = nh * q;
+    for (int j0 = threadIdx.x; j0 < total; j0 += kBlock * CH) {
+      int col[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int j = j0 + u * kBlock;
+        col[u] = j < total ? __ldg(a.hx + h0 + j / q) : 0;
+      }
+      if (vec16) {
+        const uint4* __restrict__ X4 = static_cast<const uint4*>(a.X);
+        uint4 v[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int j = j0 + u * kBlock;
+          if (j < total) v[u] = __ldg(X4 + (int64_t)col[u] * q + (j - (j / q) * q));
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int j = j0 + u * kBlock;
+          if (j < total) reinterpret_cast<uint4*>(halo_smem)[j] = v[u];
+        }
+      } else {
+        const uint32_t* __restrict__ Xw = static_cast<const uint32_t*>(a.X);
+        uint32_t v[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int j = j0 + u * kBlock;
+          if (j < total) v[u] = __ldg(Xw + (int64_t)col[u] * q + (j - (j / q) * q));
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int j = j0 + u * kBlock;
+          if (j < total) reinterpret_cast<uint32_t*>(halo_smem)[j] = v[u];
+        }
       }
     }
     __syncthreads();
-    const int r1 = min(t * a.hrows + a.hrows, a.rows);
-    for (int base = t * a.hrows; base < r1; base += rows_pb) {
+    int p = 0;
+    for (int base = r0; base < r1; base += rows_pb, ++p) {
       const int row = base + g;
       const bool live = slot_ok && row < r1;
       CT acc[CPT];
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
-      if (live) halo_row<MT, XT, CT, CPT, KL>(a, xs, __ldg(ptr + row), __ldg(ptr + row + 1), e, c0, acc);
+      for (int qq = 0; qq < CPT; ++qq) acc[qq] = (CT)0;
+      int b0 = 0, b1 = 0;
+#pragma unroll
+      for (int pp = 0; pp < MAXP; ++pp)
+        if (pp == p) {
+          b0 = kb[pp];
+          b1 = ke[pp];
+        }
+      if (p >= MAXP && live) {
+        b0 = __ldg(ptr + row);
+        b1 = __ldg(ptr + row + 1);
+      }
+      if (live) halo_row<MT, XT, CT, CPT, KL>(a, xs, b0, b1, e, c0, acc);
       if (KL > 1) {
 #pragma unroll
         for (int off = KL / 2; off >= 1; off >>= 1) {
 #pragma unroll
-          for (int q = 0; q < CPT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off * TPC);
+          for (int qq = 0; qq < CPT; ++qq) acc[qq] += __shfl_xor_sync(0xffffffffu, acc[qq], off * TPC);
         }
       }
-      if (live && e == 0) row_epilogue<XT, OT, CT, DT, CPT, false, false>(a, row, c0, acc, nullptr, dpart);
+      if (live && e == 0)
+        row_epilogue<XT, OT, CT, DT, CPT, false, false>(a, row, c0, acc, Vec<XT, CPT>{}, false, dpart);
     }
     __syncthreads();  // the next tile overwrites the halo
   }
@@ -131,8 +193,11 @@ static size_t halo_smem_bytes(VecType xt, const SpmmArgs& a) {
   return (size_t)a.hmax * (size_t)a.C * (xt == VEC_F64 ? 8 : 4);
 }
 
+// The halo form pays off only with tiles enough to fill the GPU: a tile is
+// one block's serial stage-then-compute, so a small level with a few dozen
+// tiles runs faster as the CSR kernel's many short rows.
 bool spmm_uses_halo(VecType xt, const SpmmArgs& a) {
-  return a.htiles > 0 && a.hptr && a.ndiag <= 0 && a.dot.mode == DOT_NONE && !a.imask &&
+  return a.htiles >= 2 * num_sms() && a.hptr && a.ndiag <= 0 && a.dot.mode == DOT_NONE && !a.imask &&
          halo_smem_bytes(xt, a) <= (size_t)kHaloSmemLimit;
 }
 

@@ -208,7 +208,11 @@ __device__ __forceinline__ void halo_row(const SpmmArgs& a, const XT* xs, int kb
   const MT* __restrict__ val = static_cast<const MT*>(a.val);
   const uint16_t* __restrict__ li = a.lidx;
   const int C = a.C;
-  constexpr int U = CPT >= 8 ? 2 : 4;
+  // 8 entries per lane per batch (one global round trip for the index and
+  // value loads of rows up to 8 * KL entries); each gathered row comes from
+  // shared memory right before its fmas.  The fma sequence of every lane is
+  // that of csr_row (entries in order, a masked entry adds fma(0, 0, acc)).
+  constexpr int U = 8;
   for (int k = kb + e; k < ke; k += U * KL) {
     int j[U];
     CT m[U];
@@ -218,20 +222,17 @@ __device__ __forceinline__ void halo_row(const SpmmArgs& a, const XT* xs, int kb
       j[u] = ok ? (int)__ldg(li + k + u * KL) : 0;
       m[u] = ok ? cvt<CT>(val[k + u * KL]) : (CT)0;
     }
-    Vec<XT, CPT> x[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
+      Vec<XT, CPT> x;
       if (k + u * KL < ke) {
-        x[u] = *reinterpret_cast<const Vec<XT, CPT>*>(xs + j[u] * C + c0);
+        x = *reinterpret_cast<const Vec<XT, CPT>*>(xs + j[u] * C + c0);
       } else {
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) x[u].v[q] = (XT)0;
+        for (int q = 0; q < CPT; ++q) x.v[q] = (XT)0;
       }
-    }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-#pragma unroll
-      for (int q = 0; q < CPT; ++q) acc[q] = fma(m[u], (CT)x[u].v[q], acc[q]);
+      for (int q = 0; q < CPT; ++q) acc[q] = fma(m[u], (CT)x.v[q], acc[q]);
     }
   }
 }
@@ -263,14 +264,16 @@ __device__ __forceinline__ int flag_index(const SpmmArgs& a, int row) {
 // Epilogue of one row (entry lane 0): Y = alpha acc + beta Z, the optional dot.
 template <typename XT, typename OT, typename CT, typename DT, int CPT, bool HAS_DOT, bool COH>
 __device__ __forceinline__ void row_epilogue(const SpmmArgs& a, int row, int c0, CT (&acc)[CPT],
-                                             const Vec<XT, CPT>* zpre, DT (&dpart)[CPT]) {
+                                             const Vec<XT, CPT>& zpre, bool use_zpre, DT (&dpart)[CPT]) {
   const int C = a.C;
   const CT alpha = (CT)a.alpha, beta = (CT)a.beta;
   // Y may alias Z (in-place update z += ...); each row reads Z before writing Y.
   OT* Y = static_cast<OT*>(a.Y);
   Vec<OT, CPT> out;
   if (a.beta != 0.0) {
-    const Vec<XT, CPT> zv = zpre ? *zpre : ldx<XT, CPT, COH>(static_cast<const XT*>(a.Z) + (int64_t)row * C + c0);
+    // the epilogue operand as loaded early by the caller (use_zpre), else now;
+    // passed by value so that it stays in registers
+    const Vec<XT, CPT> zv = use_zpre ? zpre : ldx<XT, CPT, COH>(static_cast<const XT*>(a.Z) + (int64_t)row * C + c0);
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const CT y = fma(alpha, acc[q], beta * (CT)zv.v[q]);
@@ -343,7 +346,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
   using DT = typename AccOf<XT>::type;  // per-thread dot partial type
   // Early epilogue-operand load only where the register budget allows it
   // without spills (the variants launched at 6 blocks per SM).
-  constexpr bool ZPF = HAS_DOT || HAS_IFACE;
+  constexpr bool ZPF = (HAS_DOT || HAS_IFACE) && !DIA;
   constexpr bool PTR_PF = ZPF && !DIA;
   const int C = a.C;
   const int TPC = C / CPT;
@@ -410,7 +413,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
     }
     lanes(acc);
     if (live && e == 0 && !flagged)
-      row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, ZPF && a.beta != 0.0 ? &zpre : nullptr,
+      row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, zpre, ZPF && a.beta != 0.0,
                                                       dpart);
   }
   if (HAS_IFACE) {
@@ -434,7 +437,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
         if (e == 0) iface_row<XT, CT, CPT, COH>(a, f, c0, acc);
       }
       lanes(acc);
-      if (live && e == 0) row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, nullptr, dpart);
+      if (live && e == 0) row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, Vec<XT, CPT>{}, false, dpart);
     }
   }
 }

@@ -5,7 +5,9 @@ halo-tiled form, and their products stage each tile's X rows in shared memory
 before gathering.  The entry lanes, batches and fma order are those of the
 CSR kernel, so a V-cycle with the halo form must give the same bits as one
 without it, in every precision, at column counts whose halos fit shared
-memory (8 columns) and at ones that fall back to the CSR kernel."""
+memory (8 columns) and at ones that fall back to the CSR kernel.  The halo
+form runs only on matrices with enough tiles to fill the GPU (two per SM),
+so the grids here are large enough for the first coarse levels to have them."""
 
 import numpy as np
 import pytest
@@ -21,7 +23,7 @@ DEV = "cuda"
 
 def _pair(N, s, **kw):
     g = gaussian_logk(N, s, seed=14, corr=3.0)
-    P = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=64, precisions=7, **kw)
+    P = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=64, precisions=7, halo_kb=64, **kw)
     Q = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=64, precisions=7, halo_kb=0, **kw)
     return P, Q
 
@@ -29,7 +31,7 @@ def _pair(N, s, **kw):
 @pytest.mark.parametrize("nrhs", [1, 4])
 @pytest.mark.parametrize("prec", [amg.PREC_FP64, amg.PREC_MIXED_FP32, amg.PREC_MIXED_BF16])
 def test_vcycle_with_halo_products_is_bit_identical(nrhs, prec):
-    N, s = (48, 40, 32), 3
+    N, s = (128, 96, 96), 3
     P, Q = _pair(N, s)
     C = nrhs << s
     dt = torch.float64 if prec == amg.PREC_FP64 else torch.float32
@@ -42,7 +44,7 @@ def test_vcycle_with_halo_products_is_bit_identical(nrhs, prec):
 
 
 def test_halo_products_are_used_and_solves_agree():
-    N, s = (64, 64, 48), 3
+    N, s = (128, 96, 96), 2
     P, Q = _pair(N, s)
     b = torch.from_numpy(rhs_uniform(P.n, 1, config=14)).to(DEV)
     recs = P.profile_step(b, torch.empty_like(b), 1, amg.PREC_MIXED_FP32)
@@ -58,7 +60,7 @@ def test_halo_products_are_used_and_solves_agree():
 
 
 def test_small_halo_budget_takes_shorter_tiles():
-    N, s = (40, 32, 32), 2
+    N, s = (128, 96, 96), 2
     g = gaussian_logk(N, s, seed=15, corr=3.0)
     Q = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=64, halo_kb=0)
     nrhs, C = 1, 1 << s
