@@ -23,6 +23,7 @@
 
 #include <algorithm>
 
+#include "coarse.cuh"
 #include "spmm_common.cuh"
 
 namespace amgsym {
@@ -59,26 +60,15 @@ __device__ __forceinline__ bool grid_barrier(const CycleBar& b) {
   return ok_s != 0;
 }
 
-// Dense coarsest solve Z = Ainv Y in FP64 arithmetic, the same two-accumulator
-// order as the stand-alone coarse kernel.
+// Dense coarsest solve Z = Ainv Y in FP64 arithmetic, the warp-per-row order
+// of the stand-alone coarse kernel (coarse.cuh).
 template <typename XT>
 __device__ __forceinline__ void dense_phase(const CoarseArgs& c) {
-  const int64_t total = (int64_t)c.n * c.C;
-  const double* __restrict__ Ainv = c.Ainv;
-  const XT* Y = static_cast<const XT*>(c.Y);  // written earlier in the launch: L2 loads
-  XT* Z = static_cast<XT*>(c.Z);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / c.C, col = t - i * c.C;
-    const double* a = Ainv + i * c.n;
-    double acc0 = 0.0, acc1 = 0.0;
-    int j = 0;
-    for (; j + 1 < c.n; j += 2) {
-      acc0 = fma(a[j], (double)ldv_cg<XT, 1>(Y + (int64_t)j * c.C + col).v[0], acc0);
-      acc1 = fma(a[j + 1], (double)ldv_cg<XT, 1>(Y + (int64_t)(j + 1) * c.C + col).v[0], acc1);
-    }
-    if (j < c.n) acc0 = fma(a[j], (double)ldv_cg<XT, 1>(Y + (int64_t)j * c.C + col).v[0], acc0);
-    Z[t] = (XT)(acc0 + acc1);
-  }
+  // Y was written earlier in the launch: L2 loads
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  coarse_rows_warp<XT>(c.n, c.C, c.Ainv, static_cast<const XT*>(c.Y), static_cast<XT*>(c.Z), warp, nwarps,
+                       [](const XT* p) { return ldv_cg<XT, 1>(p).v[0]; });
 }
 
 // Diagonal smoother step, the arithmetic of the stand-alone jacobi kernel.

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 
+#include "coarse.cuh"
 #include "device.h"
 #include "dot.cuh"
 
@@ -435,36 +436,26 @@ void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* 
 
 // ---------------------------------------------------------------------------
 // Coarsest level (Sec. 5: "a direct method solves the coarsest level"):
-// Z = A_c^{-1} Y with the precomputed FP64 inverse; FP64 arithmetic.
+// Z = A_c^{-1} Y with the precomputed FP64 inverse; FP64 arithmetic, one warp
+// per row (coarse.cuh).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) coarse_kernel(int32_t n, int32_t C, const double* __restrict__ Ainv,
                                                         const T* __restrict__ Y, T* __restrict__ Z,
                                                         const int32_t* skip) {
   if (skip && *skip == 0) return;
-  const int64_t total = (int64_t)n * C;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / C, c = t - i * C;
-    const double* a = Ainv + i * n;
-    double acc0 = 0.0, acc1 = 0.0;
-    int j = 0;
-    for (; j + 1 < n; j += 2) {
-      acc0 = fma(a[j], (double)Y[(int64_t)j * C + c], acc0);
-      acc1 = fma(a[j + 1], (double)Y[(int64_t)(j + 1) * C + c], acc1);
-    }
-    if (j < n) acc0 = fma(a[j], (double)Y[(int64_t)j * C + c], acc0);
-    Z[t] = (T)(acc0 + acc1);
-  }
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  coarse_rows_warp<T>(n, C, Ainv, Y, Z, warp, nwarps, [](const T* p) { return __ldg(p); });
 }
 
 void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
                          cudaStream_t st, const int32_t* skip) {
   count_launch();
-  const int64_t total = (int64_t)n * C;
-  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 63) / 64, max_grid_blocks()));
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n + 7) / 8, max_grid_blocks()));
   if (vt == VEC_F64)
-    coarse_kernel<double><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const double*>(Y), static_cast<double*>(Z), skip);
+    coarse_kernel<double><<<g, kBlock, 0, st>>>(n, C, Ainv, static_cast<const double*>(Y), static_cast<double*>(Z), skip);
   else
-    coarse_kernel<float><<<g, 64, 0, st>>>(n, C, Ainv, static_cast<const float*>(Y), static_cast<float*>(Z), skip);
+    coarse_kernel<float><<<g, kBlock, 0, st>>>(n, C, Ainv, static_cast<const float*>(Y), static_cast<float*>(Z), skip);
 }
 
 __global__ void hold_kernel(int32_t naps) {
