@@ -181,6 +181,12 @@ amgsym_status amgsym_create_problem(int64_t n, const int64_t* rowptr, const int3
                                     const double* vals, int32_t s, const int32_t* perm,
                                     amgsym_t* out);
 
+/* 1 if every row of the problem's operator sums to zero (relative to the
+ * row's magnitude, 1e-12), i.e. A 1 = 0: the pure Neumann problem of the
+ * paper's model problem (Sec. 2.2).  0 otherwise, -1 for a NULL handle.
+ * Such a problem is solved in the compatible sense (see amgsym_solve). */
+int32_t amgsym_is_singular(amgsym_t h);
+
 /* Sizes of a created problem (any pointer may be NULL). */
 amgsym_status amgsym_problem_sizes(amgsym_t h, int64_t* n, int64_t* n_b, int32_t* s,
                                    int64_t* nnz_inn, int64_t* n_iface_rows,
@@ -243,6 +249,18 @@ amgsym_status amgsym_level_dia(amgsym_t h, int32_t level, int32_t which, int32_t
  * and fills it.  Returns AMGSYM_NOT_CONVERGED if maxit was reached.
  * Work arrays are allocated on the device on first use for a given nrhs
  * (grow-only) and freed by amgsym_destroy.
+ *
+ * Singular problems (amgsym_is_singular, pure Neumann, Sec. 2.2 eq.
+ * "modelproblem"): the constant vector spans the null space; only the
+ * symmetric block A^_0 = A_inn + A_out,0 of the reduced system inherits it
+ * (with s >= 1, A_inn itself is regular).  The solve removes the constant
+ * component of b (the compatibility condition: a b with zero sum is left as
+ * it is; relres is measured against the compatible part), runs the same
+ * PCG -- on the consistent singular system it converges in the range of A
+ * -- and returns the solution with zero mean (the minimum-norm solution).
+ * The setup inverts a singular coarsest operator (s = 0) through the
+ * pseudo-inverse: (A_c + a 1 1^T / m)^{-1} - 1 1^T / (a m), a its mean
+ * diagonal.  Batches do not take singular problems.
  * ---------------------------------------------------------------------- */
 amgsym_status amgsym_solve(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs,
                            int64_t ld, const amgsym_solve_opts* sopts, void* stream,
@@ -380,12 +398,24 @@ amgsym_status amgsym_grid_widths(int64_t N, double gamma, double* widths_out);
 /* Number of stored entries of the 2d+1-point operator. */
 int64_t amgsym_fv_nnz(int32_t d, const int64_t* N);
 
+/* Boundary conditions of the generator: homogeneous Dirichlet on every wall
+ * (the benchmark workloads), or homogeneous Neumann on every wall -- the
+ * paper's model problem (Sec. 2.2, eq. "modelproblem"), whose operator is
+ * singular with the constant vector as null space. */
+enum { AMGSYM_BC_DIRICHLET = 0, AMGSYM_BC_NEUMANN = 1 };
+
 /* Assemble the full operator: widths = concatenation of the d per-axis width
  * arrays (host), k = per-cell coefficient (host, natural order).  Outputs are
  * caller-owned host buffers: rowptr [n+1], colidx/vals [amgsym_fv_nnz]. */
 amgsym_status amgsym_fv_assemble(int32_t d, const int64_t* N, const double* widths,
                                  const double* k, int64_t* rowptr, int32_t* colidx,
                                  double* vals);
+/* The same with boundary condition bc (AMGSYM_BC_*): a Neumann wall face
+ * carries no flux, so it adds nothing to the diagonal and every row sums to
+ * zero.  Same pattern and entry order as amgsym_fv_assemble. */
+amgsym_status amgsym_fv_assemble_bc(int32_t d, const int64_t* N, const double* widths,
+                                    const double* k, int32_t bc, int64_t* rowptr,
+                                    int32_t* colidx, double* vals);
 
 /* Mirrored-ordering map for s reflection symmetries of axes 0..s-1
  * (perm as in amgsym_create_problem, host int32 [2^s][n/2^s]). */

@@ -25,6 +25,8 @@ PREC_FP64 = 0
 PREC_MIXED_FP32 = 1
 PREC_MIXED_BF16 = 2
 
+BC = {"dirichlet": 0, "neumann": 1}
+
 STATUS = {
     0: "OK",
     1: "NOT_CONVERGED",
@@ -140,6 +142,8 @@ def _load():
         "amgsym_grid_widths": (i32, [i64, dbl, pdbl]),
         "amgsym_fv_nnz": (i64, [i32, pi64]),
         "amgsym_fv_assemble": (i32, [i32, pi64, pdbl, pdbl, pi64, pi32, pdbl]),
+        "amgsym_fv_assemble_bc": (i32, [i32, pi64, pdbl, pdbl, i32, pi64, pi32, pdbl]),
+        "amgsym_is_singular": (i32, [P]),
         "amgsym_mirror_perm": (i32, [i32, pi64, i32, pi32]),
         "amgsym_fv_grad_logk": (i32, [i32, pi64, P, P, P, P, i32, i64, P, i32, P]),
         "amgsym_kernel_launches": (i64, []),
@@ -170,7 +174,7 @@ EXPORTED = [
         "amgsym_apply_reduced amgsym_vcycle amgsym_vcycle_noalloc amgsym_grid_widths amgsym_fv_nnz "
         "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy "
         "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles amgsym_level_dia "
-        "amgsym_cycle_timeout_check amgsym_profile_step"
+        "amgsym_cycle_timeout_check amgsym_profile_step amgsym_fv_assemble_bc amgsym_is_singular"
     ).split()
 ]
 
@@ -219,8 +223,9 @@ def grid_widths(N: int, gamma: float) -> np.ndarray:
     return w
 
 
-def fv_assemble(N, widths, k):
-    """Full operator of the structured grid: (rowptr int64, colidx int32, vals f64)."""
+def fv_assemble(N, widths, k, bc: str = "dirichlet"):
+    """Full operator of the structured grid: (rowptr int64, colidx int32, vals f64);
+    bc "dirichlet" or "neumann" on every wall."""
     N = np.ascontiguousarray(N, dtype=np.int64)
     d = N.size
     nnz = lib.amgsym_fv_nnz(d, _ptr(N, ctypes.c_int64))
@@ -232,8 +237,9 @@ def fv_assemble(N, widths, k):
     rowptr = np.empty(n + 1, dtype=np.int64)
     col = np.empty(nnz, dtype=np.int32)
     val = np.empty(nnz, dtype=np.float64)
-    _check(lib.amgsym_fv_assemble(d, _ptr(N, ctypes.c_int64), _ptr(W, ctypes.c_double), _ptr(k, ctypes.c_double),
-                                  _ptr(rowptr, ctypes.c_int64), _ptr(col, ctypes.c_int32), _ptr(val, ctypes.c_double)))
+    _check(lib.amgsym_fv_assemble_bc(d, _ptr(N, ctypes.c_int64), _ptr(W, ctypes.c_double), _ptr(k, ctypes.c_double),
+                                     BC[bc], _ptr(rowptr, ctypes.c_int64), _ptr(col, ctypes.c_int32),
+                                     _ptr(val, ctypes.c_double)))
     return rowptr, col, val
 
 
@@ -274,17 +280,24 @@ class Problem:
         self.grid = None
 
     @classmethod
-    def structured(cls, N, gamma: float = 0.0, logk: Optional[np.ndarray] = None, s: int = 0):
-        """Unit-cube finite-volume problem with N cells per axis and s mirror symmetries."""
+    def structured(cls, N, gamma: float = 0.0, logk: Optional[np.ndarray] = None, s: int = 0,
+                   bc: str = "dirichlet"):
+        """Unit-cube finite-volume problem with N cells per axis and s mirror
+        symmetries; bc "dirichlet" or "neumann" (the paper's model problem)."""
         N = tuple(int(v) for v in N)
         widths = [grid_widths(n, gamma) for n in N]
         n = int(np.prod(N))
         k = np.ones(n) if logk is None else np.exp(np.asarray(logk, dtype=np.float64))
-        rowptr, col, val = fv_assemble(N, widths, k)
+        rowptr, col, val = fv_assemble(N, widths, k, bc)
         perm = mirror_perm(N, s)
         p = cls(n, rowptr, col, val, s, perm)
-        p.grid = dict(N=N, widths=widths, k=k)
+        p.grid = dict(N=N, widths=widths, k=k, bc=bc)
         return p
+
+    @property
+    def singular(self) -> bool:
+        """Every row sums to zero (pure Neumann): see amgsym_is_singular."""
+        return lib.amgsym_is_singular(self._h) == 1
 
     def close(self):
         if self._h:

@@ -588,6 +588,7 @@ static amgsym_status batch_solve_impl(Batch* B, const double* const* b_dev, doub
       fail(AMGSYM_ERR_STATE, "problem " + std::to_string(p) + " is no longer on the batch's device");
     if (D->lv.size() < 2)
       fail(AMGSYM_ERR_STATE, "problem " + std::to_string(p) + " now has a single-level hierarchy");
+    if (D->singular) fail(AMGSYM_ERR_STATE, "problem " + std::to_string(p) + " is now singular (pure Neumann)");
     if (D->nu != require_dev(B->probs[0])->nu)
       fail(AMGSYM_ERR_STATE, "the problems of a batch must use the same nu");
     BCK(cudaSetDevice(B->device_id));
@@ -798,6 +799,7 @@ extern "C" amgsym_status amgsym_batch_create(const amgsym_t* problems, int32_t c
       if (D->device_id != B->device_id) fail(AMGSYM_ERR_ARG, "all problems of a batch must be on one device");
       if (nrhs[p] < 1 || (int64_t)nrhs[p] * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
       if (D->lv.size() < 2) fail(AMGSYM_ERR_STATE, "problem " + std::to_string(p) + " has a single-level hierarchy");
+      if (D->singular) fail(AMGSYM_ERR_ARG, "problem " + std::to_string(p) + " is singular (pure Neumann): solve it alone");
       if (nu >= 0 && D->nu != nu) fail(AMGSYM_ERR_ARG, "all problems of a batch must use the same nu");
       nu = D->nu;
       B->probs.push_back(h);

@@ -205,6 +205,12 @@ void launch_jacobi(VecType vt, int64_t rows, int32_t C, const void* jd, const vo
                    cudaStream_t st, const int32_t* skip = nullptr);
 void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, const void* Y, void* Z,
                          cudaStream_t st, const int32_t* skip = nullptr);
+// Remove, for every RHS r, the mean of column r*nb of X ([rows][nrhs*nb],
+// FP64): the constant component of the natural-order vector X represents
+// (singular, pure Neumann problems).  scratch: at least (blocks + 1) * nrhs
+// doubles for up to scratch_cap / nrhs - 1 blocks.
+void launch_sub_block0_mean(double* X, int64_t rows, int32_t nrhs, int32_t nb, double* scratch,
+                            int64_t scratch_cap, cudaStream_t st);
 // A one-thread kernel that sleeps about naps x 10 us and returns (a bounded
 // loop, it waits on nothing): holds a stream while the host enqueues the
 // launches behind it, so that they then run back to back (per-launch timing).

@@ -457,11 +457,30 @@ static double lambda_max_GAGt(const Csr& A, const Csr& G, const Csr& Gt, uint64_
   return lam;
 }
 
+// Dense inverse of the coarsest operator by Cholesky.  A singular one whose
+// null space is the constant vector (every row sums to zero: the coarsest
+// level of a pure Neumann problem, whose interpolation reproduces constants)
+// gets the pseudo-inverse instead: with e = 1/sqrt(m) and a the mean
+// diagonal, B = A + a e e^T is positive definite and B^{-1} = A^+ + e e^T / a.
 static std::vector<double> dense_inverse(const Csr& A) {
   const int64_t m = A.rows;
   std::vector<double> M(m * m, 0.0);
   for (int64_t i = 0; i < m; ++i)
     for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) M[i * m + A.idx[e]] = A.val[e];
+  bool singular = m > 1;
+  double diag_mean = 0.0;
+  for (int64_t i = 0; i < m && singular; ++i) {
+    double sum = 0.0, mag = 0.0;
+    for (int64_t j = 0; j < m; ++j) {
+      sum += M[i * m + j];
+      mag += std::fabs(M[i * m + j]);
+    }
+    if (!(std::fabs(sum) <= 1e-10 * mag)) singular = false;
+    diag_mean += M[i * m + i];
+  }
+  const double shift = singular ? diag_mean / (double)m : 0.0;
+  if (singular)
+    for (int64_t i = 0; i < m * m; ++i) M[i] += shift / (double)m;
   // symmetrise (the Galerkin product is symmetric up to rounding)
   for (int64_t i = 0; i < m; ++i)
     for (int64_t j = 0; j < i; ++j) {
@@ -501,6 +520,8 @@ static std::vector<double> dense_inverse(const Csr& A) {
       const double v = 0.5 * (inv[i * m + j] + inv[j * m + i]);
       inv[i * m + j] = inv[j * m + i] = v;
     }
+  if (singular)
+    for (int64_t i = 0; i < m * m; ++i) inv[i] -= 1.0 / (shift * (double)m);
   return inv;
 }
 

@@ -89,6 +89,7 @@ struct Blocks {
   Csr Ainn;
   std::vector<int32_t> irow, icol;
   std::vector<double> ivals;
+  bool singular = false;  // every row sums to zero: the constant spans the null space
 };
 
 static Blocks extract_blocks(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* vals,
@@ -192,6 +193,18 @@ static Blocks extract_blocks(int64_t n, const int64_t* rowptr, const int32_t* co
   }
 
   Blocks B;
+  // Pure Neumann (the paper's model problem, Sec. 2.2): every row sums to
+  // zero up to rounding, so A 1 = 0 and the system is singular.
+  B.singular = true;
+  for (int64_t p = 0; p < n && B.singular; ++p) {
+    double sum = 0.0, diag = 0.0, mag = 0.0;
+    for (int64_t e = rowptr[p]; e < rowptr[p + 1]; ++e) {
+      sum += vals[e];
+      mag += std::fabs(vals[e]);
+      if (colidx[e] == p) diag = vals[e];
+    }
+    if (!(std::fabs(sum) <= 1e-12 * mag) || !(diag > 0.0)) B.singular = false;
+  }
   // Interface couplings A_out,i = sum_{m>=1} sign(i, m) H_m (eq. "hL_splitting").
   for (int64_t l = 0; l < n_b; ++l) {
     std::vector<int32_t> cols;
@@ -239,6 +252,7 @@ extern "C" amgsym_status amgsym_create_problem(int64_t n, const int64_t* rowptr,
   P->irow = std::move(B.irow);
   P->icol = std::move(B.icol);
   P->ivals = std::move(B.ivals);
+  P->singular = B.singular;
   P->perm.assign(perm, perm + n);
   // the pattern, for amgsym_update_values
   P->full_ptr.assign(rowptr, rowptr + n + 1);
@@ -261,8 +275,11 @@ extern "C" amgsym_status amgsym_update_values(amgsym_t h, const double* vals) {
   h->irow = std::move(B.irow);
   h->icol = std::move(B.icol);
   h->ivals = std::move(B.ivals);
+  h->singular = B.singular;
   API_END
 }
+
+extern "C" int32_t amgsym_is_singular(amgsym_t h) { return h ? (h->singular ? 1 : 0) : -1; }
 
 extern "C" amgsym_status amgsym_problem_sizes(amgsym_t h, int64_t* n, int64_t* n_b, int32_t* s,
                                               int64_t* nnz_inn, int64_t* n_iface_rows,
@@ -352,8 +369,17 @@ extern "C" int64_t amgsym_fv_nnz(int32_t d, const int64_t* N) {
 extern "C" amgsym_status amgsym_fv_assemble(int32_t d, const int64_t* N, const double* widths,
                                             const double* k, int64_t* rowptr, int32_t* colidx,
                                             double* vals) {
+  return amgsym_fv_assemble_bc(d, N, widths, k, AMGSYM_BC_DIRICHLET, rowptr, colidx, vals);
+}
+
+extern "C" amgsym_status amgsym_fv_assemble_bc(int32_t d, const int64_t* N, const double* widths,
+                                               const double* k, int32_t bc, int64_t* rowptr,
+                                               int32_t* colidx, double* vals) {
   API_BEGIN
   check_grid(d, N);
+  if (bc != AMGSYM_BC_DIRICHLET && bc != AMGSYM_BC_NEUMANN) fail(AMGSYM_ERR_ARG, "unknown boundary condition");
+  // a wall face carries the Dirichlet transmissibility, or no flux (Neumann)
+  const double wall = bc == AMGSYM_BC_NEUMANN ? 0.0 : 1.0;
   if (!widths || !k || !rowptr || !colidx || !vals) fail(AMGSYM_ERR_ARG, "NULL argument");
   int64_t E[3] = {1, 1, 1};
   for (int a = 0; a < d; ++a) E[a] = N[a];
@@ -395,7 +421,7 @@ extern "C" amgsym_status amgsym_fv_assemble(int32_t d, const int64_t* N, const d
             tlo[a] = area / (rq + rp);
             has_lo[a] = true;
           } else {
-            tlo[a] = area / rp;
+            tlo[a] = wall * (area / rp);
           }
           if (c[a] < E[a] - 1) {
             const int64_t q = p + stride[a];
@@ -403,7 +429,7 @@ extern "C" amgsym_status amgsym_fv_assemble(int32_t d, const int64_t* N, const d
             thi[a] = area / (rp + rq);
             has_hi[a] = true;
           } else {
-            thi[a] = area / rp;
+            thi[a] = wall * (area / rp);
           }
         }
         double diag = 0.0;

@@ -77,6 +77,7 @@ struct amgsym_problem {
   std::vector<int32_t> irow, icol;
   std::vector<double> ivals;
   std::vector<int32_t> perm;  // [nb][n_b]
+  bool singular = false;      // every row sums to zero (pure Neumann): A 1 = 0
   // the full operator's CSR pattern (natural order), kept for
   // amgsym_update_values: 8 bytes per row + 4 per stored entry
   std::vector<int64_t> full_ptr;

@@ -458,6 +458,61 @@ void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, c
     coarse_kernel<float><<<g, kBlock, 0, st>>>(n, C, Ainv, static_cast<const float*>(Y), static_cast<float*>(Z), skip);
 }
 
+// ---------------------------------------------------------------------------
+// Singular (pure Neumann) problems: the constant vector spans the null space.
+// In the reduced layout the full-grid constant is block 0 of every RHS (the
+// all-"+" combination), so removing the constant component of a natural-order
+// vector is removing the mean of its columns r*nb, r = 0..nrhs-1.
+// Deterministic: per-block partial sums in a fixed tree, one block adds the
+// partials in block order, then the subtraction.
+__global__ void __launch_bounds__(kBlock) block0_partial_kernel(const double* __restrict__ X, int64_t rows,
+                                                                int32_t C, int32_t nb, int32_t nrhs,
+                                                                double* __restrict__ part) {
+  __shared__ double sm[kBlock];
+  for (int32_t r = 0; r < nrhs; ++r) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < rows; i += (int64_t)gridDim.x * kBlock)
+      acc += X[i * C + (int64_t)r * nb];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kBlock / 2; w >= 1; w >>= 1) {
+      if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * nrhs + r] = sm[0];
+    __syncthreads();
+  }
+}
+
+__global__ void block0_mean_kernel(double* part, int32_t nblocks, int32_t nrhs, int64_t rows) {
+  for (int32_t r = threadIdx.x; r < nrhs; r += blockDim.x) {
+    double acc = 0.0;
+    for (int32_t g = 0; g < nblocks; ++g) acc += part[(int64_t)g * nrhs + r];
+    part[(int64_t)nblocks * nrhs + r] = acc / (double)rows;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) block0_sub_kernel(double* __restrict__ X, int64_t rows, int32_t C,
+                                                            int32_t nb, int32_t nrhs, const double* __restrict__ mean) {
+  const int64_t total = rows * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x; t < total; t += (int64_t)gridDim.x * kBlock) {
+    const int64_t i = t / nrhs;
+    const int32_t r = (int32_t)(t - i * nrhs);
+    X[i * C + (int64_t)r * nb] -= mean[r];
+  }
+}
+
+void launch_sub_block0_mean(double* X, int64_t rows, int32_t nrhs, int32_t nb, double* scratch,
+                            int64_t scratch_cap, cudaStream_t st) {
+  const int32_t C = nrhs * nb;
+  int64_t g = std::min<int64_t>(max_grid_blocks(), (rows + kBlock - 1) / kBlock);
+  g = std::max<int64_t>(1, std::min<int64_t>(g, scratch_cap / nrhs - 1));
+  count_launch(3);
+  block0_partial_kernel<<<(int)g, kBlock, 0, st>>>(X, rows, C, nb, nrhs, scratch);
+  block0_mean_kernel<<<1, 256, 0, st>>>(scratch, (int32_t)g, nrhs, rows);
+  block0_sub_kernel<<<grid_for(rows * nrhs, kBlock), kBlock, 0, st>>>(X, rows, C, nb, nrhs, scratch + g * nrhs);
+}
+
 __global__ void hold_kernel(int32_t naps) {
   for (int32_t i = 0; i < naps; ++i) __nanosleep(10000);
 }

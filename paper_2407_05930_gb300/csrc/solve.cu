@@ -314,6 +314,7 @@ void device_upload(amgsym_problem* p) {
   CK(cudaGetDevice(&D->device_id));
   D->precisions = p->opts.precisions | 1;  // FP64 operator always (outer residuals)
   D->nu = p->opts.nu;
+  D->singular = p->singular;
   D->s = p->s;
   D->nb = p->nb;
   D->n_b = p->n_b;
@@ -1090,6 +1091,11 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
   // Forward transform and reference norms.
   launch_transform_fwd(b_dev, nrhs, ld, D->perm, D->n_b, D->s, D->bh, VEC_F64, st);
   check_launch();
+  if (D->singular) {
+    // the compatible part of b: its constant component removed
+    launch_sub_block0_mean(D->bh, D->n_b, nrhs, D->nb, D->sc_out.partials, D->sc_out.partial_cap, st);
+    check_launch();
+  }
   DotArgs dbn = make_dot(D->sc_out, DOT_WY, FIN_STORE_BN, nullptr, nrhs, D->nb, o.tol, 0);
   launch_dot(VEC_F64, D->n_b, C, D->bh, D->bh, dbn, st);
   check_launch();
@@ -1164,6 +1170,11 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
       check_launch();
       if (breakdown) break;
     }
+  }
+  if (D->singular) {
+    // the minimum-norm solution: no constant component
+    launch_sub_block0_mean(D->xh, D->n_b, nrhs, D->nb, D->sc_out.partials, D->sc_out.partial_cap, st);
+    check_launch();
   }
   launch_transform_bwd(D->xh, VEC_F64, nrhs, D->perm, D->n_b, D->s, x_dev, ld, st);
   check_launch();

@@ -87,6 +87,7 @@ struct Device {
   std::set<std::tuple<int32_t, int, int>> tuned;  // (C, vt, mt) already tuned
   int precisions = 3;
   int nu = 1;
+  bool singular = false;  // pure Neumann: solves remove the constant component of b and x
   int32_t s = 0, nb = 1;
   int64_t n_b = 0;
   DevCsr Ainn;  // alias of lv[0].A
