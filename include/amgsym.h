@@ -266,6 +266,43 @@ amgsym_status amgsym_solve(amgsym_t h, const double* b_dev, double* x_dev, int32
                            int64_t ld, const amgsym_solve_opts* sopts, void* stream,
                            amgsym_solve_info* info);
 
+/* ------------------------------------------------------------------------
+ * LRCAMG(k) and GMRES (Sec. 2.2, Thm. "correction_nonfact", eqs. "Ydef_AMG",
+ * "LRC_AMG", "LRCAMG"; the paper's Table "lrcamg" runs GMRES with it).
+ *
+ * amgsym_lrc_setup: for every block i, the k eigenpairs (lambda_t, u_t) of
+ * X_i = M_inn^{-1} A^_i with the smallest eigenvalues, by `steps` steps of
+ * Lanczos in the A^_i inner product (full reorthogonalisation; start vector
+ * uniform[-1, 1] from `seed`), all blocks at once on the device.  The Ritz
+ * vectors u_t are A^_i-orthonormal, so v_t = A^_i u_t are the left
+ * eigenvectors with V^T U = I, and the correction of eq. "LRC_AMG" is
+ * (I + U Theta V^T) M_inn^{-1} with Theta_t = (1 - lambda_t) / lambda_t: it
+ * maps those eigenvalues of the preconditioned block to 1.  Stores U and
+ * Theta V on the device (2 k n values per block set); k = 0 removes the
+ * correction.  k in [0, 64], steps in [k, 400].  Needs amgsym_setup; a new
+ * setup discards the correction.  Synchronises the stream.
+ *
+ * amgsym_lrc_values: copies the Ritz values (host, [2^s][k], block-major)
+ * into theta (may be NULL) and returns k (0: no correction, -1: no device
+ * problem).
+ *
+ * amgsym_solve_gmres: x = A^{-1} b like amgsym_solve (same vector layout,
+ * transforms, singular handling), by restarted GMRES(restart) on the
+ * reduced system, right-preconditioned by eq. "LRCAMG": (I + U Theta V^T)
+ * (I (x) M_inn^{-1}) with use_lrc = 1, I (x) M_inn^{-1} (LRCAMG(0)) with
+ * use_lrc = 0.  Every column (block of a right-hand side) runs its own
+ * Arnoldi process with classical Gram-Schmidt and one reorthogonalisation;
+ * it stops when every RHS meets sopts->tol (the GMRES residual estimate,
+ * confirmed by the true residual at each restart) or after sopts->maxit
+ * iterations.  FP64 only (sopts->precision must be AMGSYM_PREC_FP64);
+ * sopts->finest_hat applies to the V-cycle.  info->iters = GMRES iterations.
+ * ---------------------------------------------------------------------- */
+amgsym_status amgsym_lrc_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, void* stream);
+int32_t amgsym_lrc_values(amgsym_t h, double* theta);
+amgsym_status amgsym_solve_gmres(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                                 const amgsym_solve_opts* sopts, int32_t restart, int32_t use_lrc,
+                                 void* stream, amgsym_solve_info* info);
+
 /* Adjoint solve A^T lambda = g.  A is symmetric, so this is the same reduced
  * solve; kept as its own entry point for the differentiable interface. */
 amgsym_status amgsym_solve_adjoint(amgsym_t h, const double* g_dev, double* lam_dev,

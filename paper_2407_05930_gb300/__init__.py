@@ -144,6 +144,10 @@ def _load():
         "amgsym_fv_assemble": (i32, [i32, pi64, pdbl, pdbl, pi64, pi32, pdbl]),
         "amgsym_fv_assemble_bc": (i32, [i32, pi64, pdbl, pdbl, i32, pi64, pi32, pdbl]),
         "amgsym_is_singular": (i32, [P]),
+        "amgsym_lrc_setup": (i32, [P, i32, i32, ctypes.c_uint64, P]),
+        "amgsym_lrc_values": (i32, [P, pdbl]),
+        "amgsym_solve_gmres": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), i32, i32, P,
+                                     ctypes.POINTER(SolveInfo)]),
         "amgsym_mirror_perm": (i32, [i32, pi64, i32, pi32]),
         "amgsym_fv_grad_logk": (i32, [i32, pi64, P, P, P, P, i32, i64, P, i32, P]),
         "amgsym_kernel_launches": (i64, []),
@@ -174,7 +178,8 @@ EXPORTED = [
         "amgsym_apply_reduced amgsym_vcycle amgsym_vcycle_noalloc amgsym_grid_widths amgsym_fv_nnz "
         "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy "
         "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles amgsym_level_dia "
-        "amgsym_cycle_timeout_check amgsym_profile_step amgsym_fv_assemble_bc amgsym_is_singular"
+        "amgsym_cycle_timeout_check amgsym_profile_step amgsym_fv_assemble_bc amgsym_is_singular "
+        "amgsym_lrc_setup amgsym_lrc_values amgsym_solve_gmres"
     ).split()
 ]
 
@@ -415,6 +420,42 @@ class Problem:
         _check(code)
         res = SolveResult(info.iters, info.outer_iters, bool(info.converged), rel, STATUS[code])
         return x if x.shape == b.shape else xx.reshape(b.shape), res
+
+    def lrc_setup(self, k: int, steps: int = 60, seed: int = 7):
+        """LRCAMG(k): the k smallest eigenpairs of M_inn^{-1} A^_i per block (amgsym_lrc_setup)."""
+        _check(lib.amgsym_lrc_setup(self._h, int(k), int(steps), int(seed), self._stream()))
+        return self
+
+    def lrc_values(self) -> np.ndarray:
+        """Ritz values [2^s, k] of the low-rank correction (empty without one)."""
+        k = lib.amgsym_lrc_values(self._h, None)
+        if k <= 0:
+            return np.zeros((self.nb, 0))
+        out = np.empty(self.nb * k, dtype=np.float64)
+        lib.amgsym_lrc_values(self._h, _ptr(out, ctypes.c_double))
+        return out.reshape(self.nb, k)
+
+    def solve_gmres(self, b, x=None, restart: int = 30, lrc: bool = False, **kw) -> SolveResult:
+        """Restarted GMRES with the LRCAMG preconditioner (amgsym_solve_gmres); FP64."""
+        import torch
+
+        if not (isinstance(b, torch.Tensor) and b.is_cuda and b.dtype == torch.float64):
+            raise TypeError("b must be a CUDA float64 tensor")
+        bb = b.reshape(-1, self.n).contiguous()
+        nrhs = bb.shape[0]
+        if x is None:
+            x = torch.empty_like(bb)
+        xx = x.reshape(-1, self.n)
+        o = default_solve_opts(**kw)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        info = SolveInfo()
+        info.relres = _ptr(rel, ctypes.c_double)
+        code = lib.amgsym_solve_gmres(self._h, ctypes.c_void_p(bb.data_ptr()), ctypes.c_void_p(xx.data_ptr()), nrhs,
+                                      self.n, ctypes.byref(o), int(restart), 1 if lrc else 0, self._stream(),
+                                      ctypes.byref(info))
+        _check(code)
+        res = SolveResult(info.iters, info.outer_iters, bool(info.converged), rel, STATUS[code])
+        return (x if x.shape == b.shape else xx.reshape(b.shape)), res
 
     def solve_async(self, b, x, nrhs: int, **kw) -> int:
         """Launch a solve without reading back its info (no host synchronisation

@@ -211,6 +211,18 @@ void launch_coarse_solve(VecType vt, int32_t n, int32_t C, const double* Ainv, c
 // doubles for up to scratch_cap / nrhs - 1 blocks.
 void launch_sub_block0_mean(double* X, int64_t rows, int32_t nrhs, int32_t nb, double* scratch,
                             int64_t scratch_cap, cudaStream_t st);
+// Multi-vector kernels (k_krylov.cu), FP64 [rows][C] vectors; a set V of J
+// vectors with stride vstride and Cv columns (column c pairs with c % Cv).
+// launch_mdot: H[j * C + c] = sum_rows V_j[row][c % Cv] W[row][c] (device H,
+// part: scratch of mdot_blocks(rows, C) * J * C doubles).
+int mdot_blocks(int64_t rows, int32_t C);
+void launch_mdot(const double* V, int64_t vstride, int32_t Cv, int32_t J, const double* W, int64_t rows, int32_t C,
+                 double* part, double* H, cudaStream_t st);
+// W[row][c] += sign * sum_j V_j[row][c % Cv] H[j * C + c]
+void launch_maxpy(const double* V, int64_t vstride, int32_t Cv, int32_t J, const double* H, double sign, double* W,
+                  int64_t rows, int32_t C, cudaStream_t st);
+// out[row][c] = W[row][c] s[c] (out may be W)
+void launch_colscale(const double* W, const double* s, double* out, int64_t rows, int32_t C, cudaStream_t st);
 // A one-thread kernel that sleeps about naps x 10 us and returns (a bounded
 // loop, it waits on nothing): holds a stream while the host enqueues the
 // launches behind it, so that they then run back to back (per-launch timing).

@@ -922,6 +922,11 @@ static const void* vcycle(const Ctx& c, int l, const void* y, void* z, const Dot
   });
 }
 
+void vcycle_apply(const Ctx& c, const void* R, void* Z) {
+  prepare_cycle(c);
+  vcycle(c, 0, R, Z, nullptr);
+}
+
 DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb,
                         double /*tol: the device scalar sc.tol2 holds it*/, int count_iter) {
   DotArgs d;

@@ -114,6 +114,14 @@ struct Device {
   CycleBar bar;
   int coop_ok = -1;
   std::map<CycleKey, CyclePlan> cycle_plans;
+  // Low-rank correction of LRCAMG(k) (eq. "LRCAMG"), per block i: the k
+  // right eigenvectors U of M_inn^{-1} A^_i with the smallest eigenvalues
+  // (A^_i-orthonormal) and Theta (A^_i U), both [k][n_b][nb]; Ritz values
+  // theta [nb][k] (host).  lrc_k = 0: none.
+  int32_t lrc_k = 0;
+  double* lrc_U = nullptr;
+  double* lrc_V = nullptr;
+  std::vector<double> lrc_theta;
 };
 
 struct Ctx {
@@ -165,6 +173,8 @@ void check_cycle_error(Device* D, cudaStream_t st);
 
 
 void ensure_work(Device* D, int32_t nrhs, VecType vt);
+// One V-cycle of the A_inn hierarchy: Z = (I (x) M_inn^{-1}) R (amgsym_vcycle).
+void vcycle_apply(const Ctx& c, const void* R, void* Z);
 void tune_tiles(const Ctx& c);
 Tile fixed_tile(const DevCsr& M, int32_t C, VecType xt);
 SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, const void* X,
