@@ -448,6 +448,49 @@ def run_batched(args, inline=False):
     print(json.dumps(line), flush=True)
 
 
+def run_model_tables(args):
+    """The paper's model problem (Sec. 2.2, eq. "modelproblem": Neumann on
+    every wall, 64^3 cells, tanh stretching 1.5, random compatible f):
+    iteration counts of this library's solvers next to the paper's Tables
+    "lrcamg" (GMRES + LRCAMG(k)) and "amgr"/"lrcamg" AMG rows, to relative
+    residual 1e-8.  PCG with I (x) M_inn^{-1} (s = 0: AMG of the full
+    domain) and GMRES(60) with LRCAMG(k), k = 0, 1, 2, 4, 8, 16."""
+    import torch
+
+    import paper_2407_05930_gb300 as amg
+    from oracle import fv, grid
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N = (args.model_grid,) * 3
+    h = grid.widths(N, 1.5)
+    ks = (0, 1, 2, 4, 8, 16)
+    pcg, gm, relmax = {}, {}, 0.0
+    for s in range(4):
+        P = amg.Problem.structured(N, 1.5, None, s, bc="neumann").setup()
+        f = np.random.default_rng(94).uniform(-1.0, 1.0, P.n)
+        b = f * fv.cell_volumes(h)
+        b -= b.mean()
+        bt = torch.from_numpy(b).to(dev)
+        x, info = P.solve(bt, tol=1e-8)
+        pcg[s] = info.iters
+        relmax = max(relmax, float(np.max(info.relres)))
+        row = []
+        for k in ks:
+            P.lrc_setup(k, steps=max(40, 3 * k))
+            x, info = P.solve_gmres(bt, restart=60, lrc=k > 0, tol=1e-8, maxit=400)
+            row.append(info.iters if info.converged else None)
+            relmax = max(relmax, float(np.max(info.relres)))
+        gm[s] = row
+        P.close()
+    line = {"workload": f"neumann model problem {N[0]}^3, tanh 1.5, s = 0..3, relres 1e-8",
+            "pcg_I_x_Minn": pcg, "gmres_lrcamg": {"k": list(ks), "iters_by_s": gm}, "max_relres": relmax,
+            "paper_64cube": {"gmres_AMG": [6, 6, 6, 6], "gmres_LRCAMG": {"0": [6, 23, 29, 29], "1": [9, 23, 26, 24],
+                             "2": [9, 23, 22, 24], "4": [9, 19, 21, 20], "8": [9, 17, 18, 18],
+                             "16": [9, 15, 16, 15]}, "pcg_AMGR": [6, 9, 9, 9]}}
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args):
     import torch
 
@@ -464,6 +507,8 @@ def run_gpu(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     N, s, nrhs, tol = CFG["N"], CFG["s"], args.nrhs, CFG["tol"]
 
+    if args.profile_only and args.profile_grid != N[0]:
+        N = (args.profile_grid,) * 3  # a smaller case of the same workload, for ncu pass counts
     t_setup = time.time()
     g = gaussian_logk(N, s, seed=FIELD_SEED, corr=8.0)
     P = amg.Problem.structured(N, 1.5, g, s).setup(precisions=3)
@@ -694,7 +739,9 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true", help="skip the uniform 256^3 accuracy solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload sub-object")
     ap.add_argument("--batch-steps", type=int, default=2, help="timed batched solves in the default line")
-    ap.add_argument("--workload", choices=["256cube", "batched"], default="256cube")
+    ap.add_argument("--workload", choices=["256cube", "batched", "model"], default="256cube")
+    ap.add_argument("--model-grid", type=int, default=64, help="model-problem tables: cells per axis")
+    ap.add_argument("--profile-grid", type=int, default=256, help="--profile-only: cells per axis")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--no-tune", action="store_true", help="batched: fixed tiles instead of the autotuner")
     ap.add_argument("--profile-only", choices=["mixed", "fp64", "step"], default=None,
@@ -702,6 +749,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "model":
+        run_model_tables(args)
     elif args.workload == "batched":
         import torch
 
