@@ -58,10 +58,20 @@ CPU_SAMPLE_ITERS = 200
 # the kernel sources whose SHA-256 is KERNEL_SOURCES_SHA256 (the committed
 # profile summary gives the command).  Reported as roofline.traffic only while
 # the sources are unchanged.
-PROFILED_TRAFFIC: dict = {}
+PROFILED_TRAFFIC = {
+    "spmm_kernel<float,float,float,8,4,0,0,0>": 40918095,
+    "spmm_kernel<float,float,float,8,1,0,0,1>": 162601318,
+    "spmm_kernel<float,float,float,8,1,0,0,0>": 49397102,
+    "spmm_kernel<float,float,float,8,1,1,0,1>": 277158400,
+    "spmm_kernel<float,float,float,8,1,1,1,1>": 153319168,
+    "spmm_kernel<float,float,float,4,4,0,0,0>": 9553664,
+    "cg_update1_kernel<float>": 349059840,
+    "cg_update2_kernel<float>": 152705024,
+    "coarse_kernel<float>": 94208,
+}
 KERNEL_SOURCES = ("paper_2407_05930_gb300/csrc/k_spmm.cu", "paper_2407_05930_gb300/csrc/spmm_common.cuh",
                   "paper_2407_05930_gb300/csrc/k_misc.cu", "paper_2407_05930_gb300/csrc/dot.cuh")
-KERNEL_SOURCES_SHA256 = ""
+KERNEL_SOURCES_SHA256 = "8a8f0a7540338d5c8e25bd69ec1230ad3aec8948e8365bf148a6c8dd9dd98674"
 
 
 def _kernel_sources_sha():
@@ -310,7 +320,9 @@ def _profile(P, b, x, nrhs, prec, reps=3, finest_hat=False):
 
 def _kernel_table(recs, peak):
     """Per kernel template: launches, bytes and time in one PCG iteration
-    (phase 1) and in the once-per-step part (phase 0)."""
+    (phase 1) and in the once-per-step part (phase 0); the ncu DRAM bytes per
+    launch of the committed capture while the kernel sources match it."""
+    sha_ok = bool(KERNEL_SOURCES_SHA256) and _kernel_sources_sha() == KERNEL_SOURCES_SHA256
     groups = {}
     for r in recs:
         g = groups.setdefault((r["phase"], r["kernel"]), dict(kernel=r["kernel"], phase=r["phase"], launches=0,
@@ -327,6 +339,8 @@ def _kernel_table(recs, peak):
         e = dict(kernel=g["kernel"], per="iteration" if g["phase"] == 1 else "step", launches=g["launches"],
                  algo_bytes=g["bytes"], us=round(g["us"], 2), gbs=round(gbs, 1), frac=round(gbs / peak, 3),
                  roles="; ".join(g["roles"]))
+        if g["phase"] == 1 and sha_ok and g["kernel"] in PROFILED_TRAFFIC:
+            e["dram_bytes_per_launch"] = PROFILED_TRAFFIC[g["kernel"]]
         if g["phase"] == 1:
             e["share_of_iteration"] = round(g["us"] / it_us, 3)
         out.append(e)
