@@ -127,9 +127,24 @@ typedef struct {
                                runs the CSR kernel.  Same entry and lane order as the CSR
                                kernel, so results are bit-identical.  0 = CSR only
                                (default) */
+  int32_t amgr;             /* 1: also build AMGR (Sec. 3.2), the paper's multigrid
+                               reduction, for solves with preconditioner AMGSYM_PC_AMGR:
+                               populated coarsening (Alg. "popul": the interface points and a
+                               maximal independent set of the inner points at distance
+                               amgr_distance in the strength graph, coarse in every copy),
+                               P = I (x) [W; I] with extended+i W (eq. "amgreduction"), the
+                               block-FSAI top smoother of eq. "topsmoother" (FSAI of the inner
+                               block K; the coarse block with a diagonal pattern) and a
+                               standard AMG hierarchy of A_c = P^T A P (eq. "structAc").
+                               0 (default): not built */
+  int32_t amgr_distance;    /* k of MIS(T^k) in Alg. "popul", default 2 */
+  int32_t amgr_interp_max;  /* AMGR interpolation weights kept per row, default 4 */
 } amgsym_opts;
 
 #define AMGSYM_MAX_DIAG 8
+
+/* Preconditioner of a solve (amgsym_solve_opts.preconditioner). */
+enum { AMGSYM_PC_AMG = 0, AMGSYM_PC_AMGR = 1 };
 
 typedef struct {
   double tol;          /* stop when ||b - A x||_2 / ||b||_2 <= tol per RHS, 1e-8 */
@@ -142,6 +157,9 @@ typedef struct {
   int32_t max_outer;   /* mixed: refinement steps, 20 */
   int32_t finest_hat;  /* 1: V-cycle finest-level residuals use A^_i instead of A_inn */
   int32_t use_graph;   /* 1: capture one PCG iteration in a CUDA graph and replay it */
+  int32_t preconditioner; /* AMGSYM_PC_AMG (default): I (x) M_inn^{-1}, one AMG hierarchy of
+                          A_inn for all blocks (eq. "AMGinn", LRCAMG(0)); AMGSYM_PC_AMGR: the
+                          AMGR V-cycle of Alg. "apply" (needs opts.amgr at setup) */
   int32_t tune;        /* 1: time the SpMM tile candidates of every matrix once per
                           column count and precision before the first PCG loop and
                           keep the fastest (results are then reproducible only for
@@ -380,6 +398,29 @@ typedef struct {
 amgsym_status amgsym_profile_step(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
                                   int32_t prec, int32_t finest_hat, void* stream, amgsym_prof_record* out,
                                   int32_t max_records, int32_t* count);
+
+/* AMGR (Sec. 3.2), built by amgsym_setup with opts->amgr = 1.
+ *
+ * amgsym_amgr_apply: Z = M_AMGR R, one V(1,1)-cycle of Alg. "apply" for every
+ * column (layout and arguments as amgsym_vcycle): block-FSAI smoothing
+ * (eq. "topsmoother"), residual with A^_i, restriction by P_b^T, the coarse
+ * correction through the AMG hierarchy of A_c over the full coarse domain,
+ * prolongation by P_b, block-FSAI smoothing.  AMGSYM_ERR_STATE without AMGR.
+ *
+ * amgsym_amgr_info (host; any output may be NULL): coarse points per copy
+ * (interface plus selected inner points), nonzeros of P_b and of A_c, levels
+ * of A_c's hierarchy, and the splitting cf[n_b] (1 coarse, -1 fine; int8,
+ * caller-owned).
+ *
+ * amgsym_amgr_matrix: host CSR copies (caller buffers sized from
+ * amgsym_amgr_info): which = 0 P_b (n_b x n_cb; rowptr [n_b + 1]), 1 A_c
+ * (n_cb 2^s square, row / column (l, j) at l * 2^s + j for coarse point l of
+ * copy j; rowptr [n_cb 2^s + 1]). */
+amgsym_status amgsym_amgr_apply(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs, int32_t prec,
+                                void* stream);
+amgsym_status amgsym_amgr_info(amgsym_t h, int64_t* n_coarse_per_copy, int64_t* nnz_P, int64_t* nnz_Ac,
+                               int32_t* coarse_levels, int8_t* cf);
+amgsym_status amgsym_amgr_matrix(amgsym_t h, int32_t which, int64_t* rowptr, int32_t* colidx, double* vals);
 
 /* Failure check of the persistent coarse-cycle kernel (opts->fuse_rows): runs
  * it once on the library's level work arrays with a grid barrier that awaits

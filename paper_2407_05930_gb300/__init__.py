@@ -27,6 +27,9 @@ PREC_MIXED_BF16 = 2
 
 BC = {"dirichlet": 0, "neumann": 1}
 
+PC_AMG = 0
+PC_AMGR = 1
+
 STATUS = {
     0: "OK",
     1: "NOT_CONVERGED",
@@ -67,6 +70,9 @@ class Opts(ctypes.Structure):
         ("fuse_rows", ctypes.c_int32),
         ("fsai_max_lower_coarse", ctypes.c_int32),
         ("halo_kb", ctypes.c_int32),
+        ("amgr", ctypes.c_int32),
+        ("amgr_distance", ctypes.c_int32),
+        ("amgr_interp_max", ctypes.c_int32),
     ]
 
 
@@ -80,6 +86,7 @@ class SolveOpts(ctypes.Structure):
         ("max_outer", ctypes.c_int32),
         ("finest_hat", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
+        ("preconditioner", ctypes.c_int32),
         ("tune", ctypes.c_int32),
     ]
 
@@ -145,6 +152,9 @@ def _load():
         "amgsym_fv_assemble_bc": (i32, [i32, pi64, pdbl, pdbl, i32, pi64, pi32, pdbl]),
         "amgsym_is_singular": (i32, [P]),
         "amgsym_lrc_setup": (i32, [P, i32, i32, ctypes.c_uint64, P]),
+        "amgsym_amgr_apply": (i32, [P, P, P, i32, i32, P]),
+        "amgsym_amgr_info": (i32, [P, pi64, pi64, pi64, pi32, ctypes.POINTER(ctypes.c_int8)]),
+        "amgsym_amgr_matrix": (i32, [P, i32, pi64, pi32, pdbl]),
         "amgsym_lrc_values": (i32, [P, pdbl]),
         "amgsym_solve_gmres": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), i32, i32, P,
                                      ctypes.POINTER(SolveInfo)]),
@@ -179,7 +189,8 @@ EXPORTED = [
         "amgsym_fv_assemble amgsym_mirror_perm amgsym_fv_grad_logk amgsym_kernel_launches amgsym_destroy "
         "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles amgsym_level_dia "
         "amgsym_cycle_timeout_check amgsym_profile_step amgsym_fv_assemble_bc amgsym_is_singular "
-        "amgsym_lrc_setup amgsym_lrc_values amgsym_solve_gmres"
+        "amgsym_lrc_setup amgsym_lrc_values amgsym_solve_gmres amgsym_amgr_apply amgsym_amgr_info "
+        "amgsym_amgr_matrix"
     ).split()
 ]
 
@@ -420,6 +431,35 @@ class Problem:
         _check(code)
         res = SolveResult(info.iters, info.outer_iters, bool(info.converged), rel, STATUS[code])
         return x if x.shape == b.shape else xx.reshape(b.shape), res
+
+    def amgr_info(self):
+        """AMGR sizes and splitting (amgsym_amgr_info): dict n_cb, nnz_P, nnz_Ac, levels, cf."""
+        ncb, nP, nA = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lev = ctypes.c_int32()
+        cf = np.empty(self.n_b, dtype=np.int8)
+        _check(lib.amgsym_amgr_info(self._h, ctypes.byref(ncb), ctypes.byref(nP), ctypes.byref(nA), ctypes.byref(lev),
+                                    cf.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))))
+        return dict(n_cb=ncb.value, nnz_P=nP.value, nnz_Ac=nA.value, levels=lev.value, cf=cf)
+
+    def amgr_matrix(self, which: str):
+        """Host CSR (rowptr, colidx, vals, shape) of P_b ("P") or A_c ("Ac")."""
+        info = self.amgr_info()
+        if which == "P":
+            rows, cols, nnz, w = self.n_b, info["n_cb"], info["nnz_P"], 0
+        else:
+            rows = cols = info["n_cb"] * self.nb
+            nnz, w = info["nnz_Ac"], 1
+        rp = np.empty(rows + 1, dtype=np.int64)
+        ci = np.empty(max(nnz, 1), dtype=np.int32)
+        v = np.empty(max(nnz, 1), dtype=np.float64)
+        _check(lib.amgsym_amgr_matrix(self._h, w, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32),
+                                      _ptr(v, ctypes.c_double)))
+        return rp, ci[:nnz], v[:nnz], (rows, cols)
+
+    def amgr_apply(self, R, Z, nrhs: int, prec: int = PREC_FP64):
+        _check(lib.amgsym_amgr_apply(self._h, ctypes.c_void_p(R.data_ptr()), ctypes.c_void_p(Z.data_ptr()), nrhs, prec,
+                                     self._stream()))
+        return Z
 
     def lrc_setup(self, k: int, steps: int = 60, seed: int = 7):
         """LRCAMG(k): the k smallest eigenpairs of M_inn^{-1} A^_i per block (amgsym_lrc_setup)."""

@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libamgsym.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["k_spmm.cu", "k_misc.cu", "k_batch.cu", "k_cycle.cu", "k_krylov.cu", "solve.cu", "batch.cu", "lrc.cu"]
-CXX_SOURCES = ["host_problem.cpp", "host_amg.cpp"]
+CXX_SOURCES = ["host_problem.cpp", "host_amg.cpp", "host_amgr.cpp"]
 
 
 def _nvcc() -> str:

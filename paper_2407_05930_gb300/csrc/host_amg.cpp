@@ -145,7 +145,7 @@ static inline double find(const Csr& A, int64_t r, int32_t c) {
 }
 
 // Classical strength of connection: j in S_i iff -a_ij >= theta max_{k != i} (-a_ik).
-static std::vector<uint8_t> strength(const Csr& A, double theta) {
+std::vector<uint8_t> strength(const Csr& A, double theta) {
   std::vector<uint8_t> strong(A.nnz(), 0);
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < A.rows; ++i) {
@@ -227,7 +227,7 @@ static std::vector<int8_t> pmis(const Csr& A, const std::vector<uint8_t>& strong
 // Extended+i interpolation (De Sterck, Falgout, Nolting, Yang 2008) with
 // truncation to the `max_elems` largest weights above trunc * max, rescaled
 // to keep the row sum.
-static Csr ext_i_interp(const Csr& A, const std::vector<uint8_t>& strong,
+Csr ext_i_interp(const Csr& A, const std::vector<uint8_t>& strong,
                         const std::vector<int8_t>& cf, double trunc, int max_elems) {
   const int64_t n = A.rows;
   std::vector<int32_t> cmap(n, -1);
@@ -377,7 +377,7 @@ static bool chol_solve(std::vector<double>& A, std::vector<double>& y, int m) {
 // Static FSAI: G lower triangular on the pattern {i} U (the max_lower-1
 // strongest lower entries of row i), rows scaled so diag(G A G^T) = 1
 // (eq. "Ginn": G^T G ~ A^{-1}).
-static Csr fsai(const Csr& A, int max_lower) {
+Csr fsai(const Csr& A, int max_lower) {
   const int64_t n = A.rows;
   std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
 #pragma omp parallel
@@ -433,7 +433,7 @@ static Csr fsai(const Csr& A, int max_lower) {
 
 // Largest eigenvalue of G A G^T by power iteration (an estimate from below;
 // the damping keeps a margin).
-static double lambda_max_GAGt(const Csr& A, const Csr& G, const Csr& Gt, uint64_t seed) {
+double lambda_max_GAGt(const Csr& A, const Csr& G, const Csr& Gt, uint64_t seed) {
   const int64_t n = A.rows;
   std::vector<double> v(n), t1, t2, t3;
   std::mt19937_64 rng(seed ^ 0x9e3779b97f4a7c15ULL);
@@ -718,6 +718,8 @@ extern "C" amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts) {
   if (o.coarse_max < 1 || o.coarse_max > kDenseLimit) fail(AMGSYM_ERR_ARG, "coarse_max out of range");
   if (o.max_levels < 1) fail(AMGSYM_ERR_ARG, "max_levels must be >= 1");
   if ((o.precisions & 7) == 0) fail(AMGSYM_ERR_ARG, "precisions mask is empty");
+  if (o.amgr && (o.amgr_distance < 1 || o.amgr_distance > 4 || o.amgr_interp_max < 1))
+    fail(AMGSYM_ERR_ARG, "amgr_distance must be in [1, 4] and amgr_interp_max >= 1");
   device_free(h);
   h->have_hierarchy = false;
   h->opts = o;
@@ -727,6 +729,8 @@ extern "C" amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts) {
     L.Gdia = build_dia(L.G, o.dia_max_diag);
     L.Gtdia = build_dia(L.Gt, o.dia_max_diag);
   }
+  h->amgr.reset();
+  if (o.amgr) build_amgr(h, o);
   h->have_hierarchy = true;
   if (!o.host_only) device_upload(h);
   API_END

@@ -63,6 +63,9 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->fuse_rows = 0;
   o->fsai_max_lower_coarse = 1;
   o->halo_kb = 0;
+  o->amgr = 0;
+  o->amgr_distance = 2;
+  o->amgr_interp_max = 4;
 }
 
 extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {
@@ -75,6 +78,7 @@ extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {
   o->max_outer = 20;
   o->finest_hat = 0;
   o->use_graph = 1;
+  o->preconditioner = AMGSYM_PC_AMG;
   o->tune = 0;
 }
 
@@ -271,6 +275,7 @@ extern "C" amgsym_status amgsym_update_values(amgsym_t h, const double* vals) {
   device_free(h);
   h->have_hierarchy = false;
   h->H = HostHierarchy();
+  h->amgr.reset();
   h->Ainn = std::move(B.Ainn);
   h->irow = std::move(B.irow);
   h->icol = std::move(B.icol);

@@ -64,6 +64,24 @@ struct HostHierarchy {
 
 struct Device;  // device-resident copies and work arrays (solve.cu)
 
+// AMGR (Sec. 3.2): the multigrid reduction of the full operator.  Populated
+// coarsening (Alg. "popul"): every interface point of the base mesh (a row
+// coupled to another mirror copy) and a maximal independent set of the inner
+// points at distance k in the strength graph are coarse, in every copy; the
+// prolongation is I (x) P_b with P_b = [W; I] (eq. "amgreduction"); the
+// top-level smoother is the block FSAI of eq. "topsmoother"; the reduced
+// operator A_c = P^T A P (eq. "structAc") gets a standard AMG hierarchy.
+struct HostAmgr {
+  std::vector<int8_t> cf;   // per base row: 1 coarse (interface or selected inner), -1 fine
+  int32_t n_cb = 0;         // coarse points per copy
+  Csr Pb, Rb;               // n_b x n_cb prolongation of one copy, and its transpose
+  Csr GK, GKt;              // FSAI of K = A_inn[F, F], embedded in n_b x n_b (fine rows and columns)
+  double omegaK = 1.0;      // damping of the fine-point smoother
+  std::vector<double> jdC;  // coarse rows: omega_C / a_ll (the FSAI of C-bar with a diagonal pattern); fine rows 0
+  Csr Ac;                   // full reduced operator, n_cb * 2^s rows, copy index fastest
+  std::shared_ptr<amgsym_problem> coarse;  // Ac with its AMG hierarchy (and device copies)
+};
+
 }  // namespace amgsym
 
 struct amgsym_problem {
@@ -85,12 +103,24 @@ struct amgsym_problem {
   amgsym_opts opts{};
   bool have_hierarchy = false;
   amgsym::HostHierarchy H;
+  std::shared_ptr<amgsym::HostAmgr> amgr;  // AMGR top level (opts.amgr)
   amgsym::Device* dev = nullptr;
 };
 
 namespace amgsym {
 // host_amg.cpp
 void build_hierarchy(const Csr& A, const amgsym_opts& o, HostHierarchy& H);
+// classical strength: strong[e] = 1 when -a_ij >= theta max_k (-a_ik) (entry e = (i, j))
+std::vector<uint8_t> strength(const Csr& A, double theta);
+// extended+i interpolation for the splitting cf (1 = C, -1 = F), truncated
+Csr ext_i_interp(const Csr& A, const std::vector<uint8_t>& strong, const std::vector<int8_t>& cf, double trunc,
+                 int max_elems);
+// static FSAI factor G (G^T G ~ A^{-1}) on the strongest lower pattern
+Csr fsai(const Csr& A, int max_lower);
+// power-iteration estimate of lambda_max(G A G^T)
+double lambda_max_GAGt(const Csr& A, const Csr& G, const Csr& Gt, uint64_t seed);
+// host_amgr.cpp
+void build_amgr(amgsym_problem* p, const amgsym_opts& o);
 Csr transpose(const Csr& A);
 Csr spgemm(const Csr& A, const Csr& B);
 void sort_rows(Csr& A);

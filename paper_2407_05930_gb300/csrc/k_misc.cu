@@ -513,6 +513,47 @@ void launch_sub_block0_mean(double* X, int64_t rows, int32_t nrhs, int32_t nb, d
   block0_sub_kernel<<<grid_for(rows * nrhs, kBlock), kBlock, 0, st>>>(X, rows, C, nb, nrhs, scratch + g * nrhs);
 }
 
+// ---------------------------------------------------------------------------
+// AMGR coarse step: between the transformed layout of Alg. 1 ([n_cb][nrhs *
+// 2^s], column r * 2^s + i = block i) and the full coarse domain of the
+// coarse problem ([n_cb * 2^s][nrhs], row l * 2^s + j = copy j), by the
+// Walsh-Hadamard butterfly of eq. "P_s": out_j = scale * sum_i s(i, j) in_i
+// with s(i, j) = (-1)^popcount(i & j) (dir 0: scale 2^-s; dir 1: scale 1).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) coarse_relayout_kernel(const T* __restrict__ in, T* __restrict__ out,
+                                                                 int64_t ncb, int32_t nrhs, int32_t nb, int dir) {
+  const int64_t total = ncb * nrhs;
+  const double scale = dir == 0 ? 1.0 / nb : 1.0;
+  for (int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x; t < total; t += (int64_t)gridDim.x * kBlock) {
+    const int64_t l = t / nrhs;
+    const int32_t r = (int32_t)(t - l * nrhs);
+    double v[16];
+    for (int32_t i = 0; i < nb; ++i)
+      v[i] = dir == 0 ? (double)in[l * nrhs * nb + (int64_t)r * nb + i] : (double)in[(l * nb + i) * nrhs + r];
+    for (int32_t j = 0; j < nb; ++j) {
+      double acc = 0.0;
+      for (int32_t i = 0; i < nb; ++i) acc += (__popc((unsigned)(i & j)) & 1) ? -v[i] : v[i];
+      const T o = (T)(scale * acc);
+      if (dir == 0)
+        out[(l * nb + j) * nrhs + r] = o;
+      else
+        out[l * nrhs * nb + (int64_t)r * nb + j] = o;
+    }
+  }
+}
+
+void launch_coarse_relayout(VecType vt, const void* in, void* out, int64_t ncb, int32_t nrhs, int32_t nb, int dir,
+                            cudaStream_t st) {
+  count_launch();
+  const int g = grid_for(ncb * nrhs, kBlock);
+  if (vt == VEC_F64)
+    coarse_relayout_kernel<double><<<g, kBlock, 0, st>>>(static_cast<const double*>(in), static_cast<double*>(out),
+                                                         ncb, nrhs, nb, dir);
+  else
+    coarse_relayout_kernel<float><<<g, kBlock, 0, st>>>(static_cast<const float*>(in), static_cast<float*>(out), ncb,
+                                                        nrhs, nb, dir);
+}
+
 __global__ void hold_kernel(int32_t naps) {
   for (int32_t i = 0; i < naps; ++i) __nanosleep(10000);
 }

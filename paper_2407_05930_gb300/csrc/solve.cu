@@ -80,6 +80,13 @@ static std::string matrix_name(const Device* D, const DevCsr& M, int* level) {
     if (M.idx == L.G.idx) return "G";
     if (M.idx == L.Gt.idx) return "Gt";
   }
+  *level = 0;
+  if (D->has_amgr) {
+    if (M.idx == D->amgr.Pb.idx) return "AMGR P_b";
+    if (M.idx == D->amgr.Rb.idx) return "AMGR R_b";
+    if (M.idx == D->amgr.GK.idx) return "AMGR G_K";
+    if (M.idx == D->amgr.GKt.idx) return "AMGR G_K^T";
+  }
   *level = -1;
   return "?";
 }
@@ -293,6 +300,7 @@ static void free_work(Device* D) {
 }
 
 void device_free(amgsym_problem* p) {
+  if (p->amgr && p->amgr->coarse) device_free(p->amgr->coarse.get());
   Device* D = p->dev;
   if (!D) return;
   cudaSetDevice(D->device_id);
@@ -383,6 +391,27 @@ void device_upload(amgsym_problem* p) {
     std::vector<float> v32(p->ivals.begin(), p->ivals.end());
     D->iface.ival32 = upload(D->owned, v32.data(), ne * p->nb);
   }
+  // AMGR top level and its coarse problem
+  if (p->amgr) {
+    const HostAmgr& M = *p->amgr;
+    DevAmgr& G = D->amgr;
+    const int hk = p->opts.halo_kb;
+    G.Pb = upload_csr(D->owned, M.Pb, D->precisions, nullptr, hk);
+    G.Rb = upload_csr(D->owned, M.Rb, D->precisions, nullptr, hk);
+    G.GK = upload_csr(D->owned, M.GK, D->precisions, nullptr, hk);
+    G.GKt = upload_csr(D->owned, M.GKt, D->precisions, nullptr, hk);
+    G.omegaK = M.omegaK;
+    G.n_cb = M.n_cb;
+    G.jd64 = upload(D->owned, M.jdC.data(), (int64_t)M.jdC.size());
+    std::vector<float> j32(M.jdC.begin(), M.jdC.end());
+    G.jd32 = upload(D->owned, j32.data(), (int64_t)j32.size());
+    amgsym_problem* cp = M.coarse.get();
+    cp->opts.precisions = D->precisions;
+    device_upload(cp);
+    CK(cudaSetDevice(D->device_id));
+    G.cd = cp->dev;
+    D->has_amgr = true;
+  }
   // persistent coarse cycle from the first level below the finest with at
   // most fuse_rows rows (only when it leaves at least one product to fuse)
   D->fuse_level = -1;
@@ -462,6 +491,15 @@ void ensure_work(Device* D, int32_t nrhs, VecType vt) {
   W.z = vec(D->n_b);
   W.p = vec(D->n_b);
   W.q = vec(D->n_b);
+  if (D->has_amgr) {
+    W.at = vec(D->n_b);
+    W.ar = vec(D->n_b);
+    W.arc = vec(D->amgr.n_cb);
+    W.ahc = vec(D->amgr.n_cb);
+    W.arc2 = vec(D->amgr.n_cb);  // n_cb * 2^s rows x nrhs columns: the same size
+    W.ahc2 = vec(D->amgr.n_cb);
+    ensure_work(D->amgr.cd, D->work_nrhs, vt);
+  }
   // FP64 PCG iterates on x^ itself; the FP32 inner PCG on its own correction.
   W.x = vt == VEC_F64 ? (void*)D->xh : vec(D->n_b);
   W.ready = true;
@@ -927,6 +965,55 @@ void vcycle_apply(const Ctx& c, const void* R, void* Z) {
   vcycle(c, 0, R, Z, nullptr);
 }
 
+// AMGR V(1,1) of Alg. "apply" in the transformed basis: every operator of
+// its first level is the same for all 2^s blocks (P = I (x) P_b, the block
+// FSAI smoother of eq. "topsmoother"), the residuals use A^_i, and the coarse
+// correction solves A_c over the full coarse domain with its AMG hierarchy.
+void amgr_apply(const Ctx& c, const void* y, void* z) {
+  Device* D = c.D;
+  const DevAmgr& M = D->amgr;
+  PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
+  const ValType mt = c.mt;
+  const VecType vt = c.vt;
+  const int32_t nrhs = c.C / D->nb;
+  auto smooth = [&](const void* src, double beta) {  // z = beta z + S src
+    spmm(c, M.GK, mt, vt, vt, src, W.at, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, M.GKt, mt, vt, vt, W.at, z, M.omegaK, beta, z, false, nullptr);
+    ProfScope ps(c.st);
+    launch_jacobi(vt, D->n_b, c.C, M.jd(vt), src, z, 1, c.st, c.skip);
+    check_launch();
+    if (ps.on())
+      ps.end(std::string("jacobi_kernel<") + tname(vt) + ">", "AMGR coarse-point smoother", 0,
+             xsize(vt) * D->n_b * (1 + 3 * (int64_t)c.C));
+  };
+  smooth(y, 0.0);  // presmoothing from zero
+  spmm(c, D->Ainn, mt, vt, vt, z, W.ar, -1.0, 1.0, y, true, nullptr);  // r = y - A^ z
+  spmm(c, M.Rb, mt, vt, vt, W.ar, W.arc, 1.0, 0.0, nullptr, false, nullptr);
+  launch_coarse_relayout(vt, W.arc, W.arc2, M.n_cb, nrhs, D->nb, 0, c.st);
+  check_launch();
+  Ctx cc{M.cd, nrhs, vt, mt, false, c.st};
+  cc.skip = c.skip;
+  const void* hc2 = vcycle(cc, 0, W.arc2, W.ahc2, nullptr);
+  launch_coarse_relayout(vt, hc2, W.ahc, M.n_cb, nrhs, D->nb, 1, c.st);
+  check_launch();
+  spmm(c, M.Pb, mt, vt, vt, W.ahc, z, 1.0, 1.0, z, false, nullptr);  // z += P h_c
+  spmm(c, D->Ainn, mt, vt, vt, z, W.ar, -1.0, 1.0, y, true, nullptr);
+  smooth(W.ar, 1.0);  // postsmoothing
+}
+
+// The preconditioner step of the PCG: z = M r with <r, z> (dot `d`).
+static void precondition(const Ctx& c, const void* r, void* z, const DotArgs* d) {
+  if (c.pc == AMGSYM_PC_AMGR) {
+    amgr_apply(c, r, z);
+    ProfScope ps(c.st);
+    launch_dot(c.vt, c.D->n_b, c.C, r, z, *d, c.st, c.skip);
+    check_launch();
+    if (ps.on()) ps.end(std::string("dot_kernel<") + tname(c.vt) + ">", "<r,z>", -1, 2 * xsize(c.vt) * c.D->n_b * c.C);
+    return;
+  }
+  vcycle(c, 0, r, z, d);
+}
+
 DotArgs make_dot(const DevScalars& sc, int mode, int final, const void* W, int32_t nrhs, int32_t nb,
                         double /*tol: the device scalar sc.tol2 holds it*/, int count_iter) {
   DotArgs d;
@@ -957,7 +1044,7 @@ static void pcg_iteration(const Ctx& c, PrecWork& W, const DevScalars& sc, int32
              6 * xsize(c.vt) * D->n_b * c.C);
   }
   DotArgs drz = make_dot(sc, DOT_WY, FIN_BETA, W.r, nrhs, D->nb, tol, 0);
-  vcycle(c, 0, W.r, W.z, &drz);
+  precondition(c, W.r, W.z, &drz);
   {
     ProfScope ps(c.st);
     launch_cg_update2(c.vt, D->n_b, c.C, W.p, W.z, sc.beta, c.st, c.skip);
@@ -991,7 +1078,7 @@ static int pcg_loop(const Ctx& c0, PrecWork& W, const DevScalars& sc, int32_t nr
   graph_key.tiles_gen = D->tiles_gen;
   // start: z = M r, rz, p = z
   DotArgs drz = make_dot(sc, DOT_WY, FIN_STORE_RZ, W.r, nrhs, D->nb, tol, 0);
-  vcycle(c, 0, W.r, W.z, &drz);
+  precondition(c, W.r, W.z, &drz);
   launch_copy(c.vt, D->n_b * c.C, W.p, W.z, c.st);
   check_launch();
   cudaGraphExec_t exec = nullptr;
@@ -1085,11 +1172,16 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
   const ValType vmt = o.precision == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : mixed ? VAL_F32 : VAL_F64;
   if (mixed && !(h->opts.precisions & (o.precision == AMGSYM_PREC_MIXED_BF16 ? 4 : 2)))
     fail(AMGSYM_ERR_STATE, "setup did not build the value precision this mode needs (opts.precisions)");
+  if (o.preconditioner != AMGSYM_PC_AMG && o.preconditioner != AMGSYM_PC_AMGR)
+    fail(AMGSYM_ERR_ARG, "unknown preconditioner");
+  if (o.preconditioner == AMGSYM_PC_AMGR && !D->has_amgr)
+    fail(AMGSYM_ERR_STATE, "AMGR was not built: call amgsym_setup with opts.amgr = 1");
   ensure_work(D, nrhs, vt);
   const int32_t C = nrhs * D->nb;
   Ctx c{D, C, vt, vmt, o.finest_hat != 0, st};
   c.tune = o.tune != 0;
   c.fuse = true;
+  c.pc = o.preconditioner;
   Ctx c64{D, C, VEC_F64, VAL_F64, false, st};
   // 64-bit work is needed for the FP64 path; the mixed path uses bh/xh only.
   PrecWork& W = mixed ? D->w32 : D->w64;
@@ -1129,7 +1221,7 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
       read_status(D, D->sc_out, st, st4);
       if (st4[0] == 0 || total_it >= o.maxit) break;
       const int it = pcg_loop(c, W, D->sc_out, nrhs, o.tol, o.maxit - total_it, graphs,
-                              0x100 | (o.finest_hat ? 1 : 0), &breakdown);
+                              0x100 | (o.finest_hat ? 1 : 0) | (o.preconditioner << 4), &breakdown);
       total_it += it;
       if (breakdown) break;
     }
@@ -1168,7 +1260,8 @@ static amgsym_status solve_impl(amgsym_t h, const double* b_dev, double* x_dev, 
       launch_zero(VEC_F32, D->n_b * C, W.x, st);
       check_launch();
       const int it = pcg_loop(c, W, D->sc_in, nrhs, o.inner_tol, o.maxit - total_it, graphs,
-                              0x200 | (o.precision == AMGSYM_PREC_MIXED_BF16 ? 2 : 0) | (o.finest_hat ? 1 : 0),
+                              0x200 | (o.precision == AMGSYM_PREC_MIXED_BF16 ? 2 : 0) | (o.finest_hat ? 1 : 0) |
+                                  (o.preconditioner << 4),
                               &breakdown);
       total_it += it;
       launch_add_to_f64(VEC_F32, D->n_b * C, D->xh, W.x, st);
@@ -1290,6 +1383,53 @@ extern "C" amgsym_status amgsym_vcycle(amgsym_t h, const void* R_dev, void* Z_de
   c.fuse = true;
   prepare_cycle(c);
   vcycle(c, 0, R_dev, Z_dev, nullptr);
+  API_END
+}
+
+extern "C" amgsym_status amgsym_amgr_apply(amgsym_t h, const void* R_dev, void* Z_dev, int32_t nrhs, int32_t prec,
+                                           void* stream) {
+  API_BEGIN
+  Device* D = require_dev(h);
+  if (!D->has_amgr) fail(AMGSYM_ERR_STATE, "AMGR was not built: call amgsym_setup with opts.amgr = 1");
+  if (nrhs < 1 || (int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
+  check_ptr(R_dev, "R");
+  check_ptr(Z_dev, "Z");
+  if (R_dev == Z_dev) fail(AMGSYM_ERR_ARG, "R and Z must not overlap");
+  const bool f64 = prec == AMGSYM_PREC_FP64;
+  const VecType vt = f64 ? VEC_F64 : VEC_F32;
+  const ValType mt = f64 ? VAL_F64 : prec == AMGSYM_PREC_MIXED_BF16 ? VAL_BF16 : VAL_F32;
+  if (!D->Ainn.vals(mt)) fail(AMGSYM_ERR_STATE, "value precision not built");
+  ensure_work(D, nrhs, vt);
+  Ctx c{D, nrhs * D->nb, vt, mt, false, (cudaStream_t)stream};
+  c.pc = AMGSYM_PC_AMGR;
+  amgr_apply(c, R_dev, Z_dev);
+  API_END
+}
+
+extern "C" amgsym_status amgsym_amgr_info(amgsym_t h, int64_t* n_coarse_per_copy, int64_t* nnz_P, int64_t* nnz_Ac,
+                                          int32_t* coarse_levels, int8_t* cf) {
+  API_BEGIN
+  if (!h) fail(AMGSYM_ERR_ARG, "NULL handle");
+  if (!h->amgr) fail(AMGSYM_ERR_STATE, "AMGR was not built: call amgsym_setup with opts.amgr = 1");
+  const HostAmgr& M = *h->amgr;
+  if (n_coarse_per_copy) *n_coarse_per_copy = M.n_cb;
+  if (nnz_P) *nnz_P = M.Pb.nnz();
+  if (nnz_Ac) *nnz_Ac = M.Ac.nnz();
+  if (coarse_levels) *coarse_levels = (int32_t)M.coarse->H.levels.size();
+  if (cf) std::memcpy(cf, M.cf.data(), M.cf.size());
+  API_END
+}
+
+extern "C" amgsym_status amgsym_amgr_matrix(amgsym_t h, int32_t which, int64_t* rowptr, int32_t* colidx,
+                                            double* vals) {
+  API_BEGIN
+  if (!h || !rowptr || !colidx || !vals) fail(AMGSYM_ERR_ARG, "NULL argument");
+  if (!h->amgr) fail(AMGSYM_ERR_STATE, "AMGR was not built: call amgsym_setup with opts.amgr = 1");
+  if (which != 0 && which != 1) fail(AMGSYM_ERR_ARG, "which must be 0 (P_b) or 1 (A_c)");
+  const Csr& M = which == 0 ? h->amgr->Pb : h->amgr->Ac;
+  std::memcpy(rowptr, M.ptr.data(), sizeof(int64_t) * M.ptr.size());
+  std::memcpy(colidx, M.idx.data(), sizeof(int32_t) * M.idx.size());
+  std::memcpy(vals, M.val.data(), sizeof(double) * M.val.size());
   API_END
 }
 

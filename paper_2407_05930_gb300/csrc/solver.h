@@ -38,6 +38,10 @@ struct PrecWork {
   bool ready = false;
   std::vector<LevelWork> lw;
   void *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *x = nullptr;  // PCG vectors
+  // AMGR V-cycle: smoother temporary and residual [n_b][C], restricted
+  // residual and coarse correction [n_cb][C], the same in the coarse
+  // problem's layout [n_cb * 2^s][nrhs]
+  void *at = nullptr, *ar = nullptr, *arc = nullptr, *ahc = nullptr, *arc2 = nullptr, *ahc2 = nullptr;
 };
 
 struct GraphKey {
@@ -77,6 +81,19 @@ using TileKey = std::tuple<const void*, int32_t, int, int, int>;  // matrix idx 
 // repeats its generations (a batch compares them to decide whether its plans,
 // which hold device pointers, are still valid).
 uint64_t next_generation();
+
+// AMGR top level on the device (see HostAmgr): P_b, R_b = P_b^T, the FSAI of
+// the inner block K (embedded, fine rows), its damping, the coarse-row
+// diagonal smoother, and the coarse problem A_c with its own hierarchy.
+struct DevAmgr {
+  DevCsr Pb, Rb, GK, GKt;
+  double omegaK = 1.0;
+  double* jd64 = nullptr;
+  float* jd32 = nullptr;
+  int32_t n_cb = 0;
+  Device* cd = nullptr;  // the coarse problem's device copy (owned by that problem)
+  const void* jd(VecType t) const { return t == VEC_F64 ? (const void*)jd64 : (const void*)jd32; }
+};
 
 struct Device {
   int device_id = 0;
@@ -122,6 +139,8 @@ struct Device {
   double* lrc_U = nullptr;
   double* lrc_V = nullptr;
   std::vector<double> lrc_theta;
+  bool has_amgr = false;
+  DevAmgr amgr;
 };
 
 struct Ctx {
@@ -134,7 +153,10 @@ struct Ctx {
   const int32_t* skip = nullptr;  // early-exit flag (active RHS count) of the PCG loop
   bool tune = false;              // run the tile autotuner before the first PCG loop
   bool fuse = false;              // coarse levels as one persistent kernel (Device::fuse_level)
+  int pc = AMGSYM_PC_AMG;         // preconditioner of the PCG: the A_inn V-cycle or AMGR
 };
+// The AMGR V-cycle (Alg. "apply"): z = M_AMGR y for every column of c.
+void amgr_apply(const Ctx& c, const void* y, void* z);
 
 // ---------------------------------------------------------------------------
 // Per-launch timing (amgsym_profile_step): while a Profiler is installed for

@@ -1,0 +1,101 @@
+"""AMGR setup on the host (Sec. 3.2; CPU only): the populated coarsening of
+Alg. "popul", the prolongation of eq. "amgreduction" and the reduced operator
+of eq. "structAc", checked against their definitions with the oracle's
+operator.
+
+* every interface point (a base row coupled to another mirror copy) is
+  coarse; the selected inner points are independent at distance k in the
+  strength graph of the inner points, and maximal (every inner fine point
+  lies within distance k of one);
+* P_b = [W; I]: a unit row per coarse point, and the fine rows of a
+  zero-row-sum row of A_inn interpolate constants exactly;
+* A_c = P^T A P with P = I (x) P_b, computed from the full unreduced
+  operator in the mirrored order, equals the library's A_c.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import shortest_path
+
+import paper_2407_05930_gb300 as amg
+from oracle import fv, grid, symmetry
+from synth import gaussian_logk
+
+
+def _strength(A, theta=0.25):
+    """Classical strength of connection by its definition: j strong for i
+    when -a_ij >= theta * max_{k != i} (-a_ik)."""
+    A = A.tocsr()
+    rows, cols = [], []
+    for i in range(A.shape[0]):
+        lo, hi = A.indptr[i], A.indptr[i + 1]
+        c, v = A.indices[lo:hi], A.data[lo:hi]
+        off = c != i
+        if not np.any(off):
+            continue
+        mx = np.max(-v[off])
+        if mx <= 0:
+            continue
+        for j, a in zip(c[off], v[off]):
+            if -a >= theta * mx:
+                rows.append(i)
+                cols.append(j)
+    return sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=A.shape)
+
+
+@pytest.mark.parametrize("N,s,bc,k", [((16, 12, 10), 1, "dirichlet", 2), ((12, 12, 8), 2, "neumann", 2),
+                                      ((12, 8, 8), 3, "dirichlet", 2), ((14, 10, 8), 1, "dirichlet", 3)])
+def test_populated_coarsening_prolongation_and_reduced_operator(N, s, bc, k):
+    g = gaussian_logk(N, s, seed=31, corr=2.0)
+    A = fv.assemble(grid.widths(N, 1.5), np.exp(g), bc)
+    perm = symmetry.mirror_perm(N, s)
+    P = amg.Problem(A.shape[0], A.indptr, A.indices, A.data, s, perm)
+    P.setup(host_only=1, amgr=1, amgr_distance=k, coarse_max=64)
+    info = P.amgr_info()
+    cf = info["cf"]
+    H = symmetry.blocks(A, perm)
+    Ainn = H[0].tocsr()
+    nb = 1 << s
+    # interface: rows of the base block coupled to another copy
+    iface = np.zeros(Ainn.shape[0], bool)
+    for m in range(1, nb):
+        iface |= np.diff(H[m].tocsr().indptr) > 0
+    assert np.all(cf[iface] == 1)
+    inner = ~iface
+    # the strength graph of the inner points, symmetrised, and distances in it
+    S = _strength(Ainn)
+    T = ((S + S.T) > 0).astype(float)
+    T = T[inner][:, inner]
+    D = shortest_path(T, unweighted=True, directed=False)
+    sel = cf[inner] == 1
+    Dsel = D[np.ix_(sel, sel)]
+    np.fill_diagonal(Dsel, np.inf)
+    assert np.all(Dsel > k)  # independent at distance k
+    assert np.all(np.min(D[:, sel], axis=1)[~sel] <= k)  # maximal
+    # P_b = [W; I]
+    rp, ci, v, shape = P.amgr_matrix("P")
+    Pb = sp.csr_matrix((v, ci, rp), shape=shape)
+    assert shape == (Ainn.shape[0], info["n_cb"]) and info["n_cb"] == int(np.sum(cf == 1))
+    cidx = np.cumsum(cf == 1) - 1
+    for i in np.flatnonzero(cf == 1):
+        row = Pb.getrow(i)
+        assert row.nnz == 1 and row.indices[0] == cidx[i] and row.data[0] == 1.0
+    rowsum = np.asarray(Ainn.sum(axis=1)).ravel()
+    diag = Ainn.diagonal()
+    zero = (np.abs(rowsum) <= 1e-12 * diag) & (cf == -1) & (np.diff(Pb.indptr) > 0)
+    assert np.any(zero)
+    assert np.max(np.abs(np.asarray(Pb[zero].sum(axis=1)).ravel() - 1.0)) <= 1e-12
+    # A_c = P^T A P in the interleaved mirrored order (base point l, copy j -> l * nb + j)
+    n_b = Ainn.shape[0]
+    order = np.empty(A.shape[0], dtype=np.int64)
+    for j in range(nb):
+        order[np.arange(n_b) * nb + j] = perm[j]
+    Am = A[order][:, order]
+    Pfull = sp.kron(Pb, sp.identity(nb), format="csr")
+    Ac_ref = (Pfull.T @ Am @ Pfull).tocsr()
+    rp, ci, v, shape = P.amgr_matrix("Ac")
+    Ac = sp.csr_matrix((v, ci, rp), shape=shape)
+    assert shape == Ac_ref.shape
+    assert abs(Ac - Ac_ref).max() <= 1e-12 * abs(Ac_ref).max()
+    assert info["levels"] >= 1
