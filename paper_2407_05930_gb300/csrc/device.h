@@ -118,6 +118,10 @@ enum DotMode { DOT_NONE = 0, DOT_WY = 1, DOT_YY = 2 };
 struct DotArgs {
   int32_t mode = DOT_NONE;
   int32_t final = FIN_NONE;
+  // 1: the blocks of a right-hand side are coupled (a preconditioner that is
+  // not block diagonal in the transformed basis, AMGR): the CG scalars of
+  // every column come from the sum over its RHS's 2^s columns (one CG per RHS)
+  int32_t coupled = 0;
   const void* W = nullptr;  // partner vector for DOT_WY (XT layout [rows][C])
   DevScalars sc;
   ConvParams cp{};

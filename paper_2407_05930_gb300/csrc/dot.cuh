@@ -166,6 +166,15 @@ __device__ __forceinline__ void block_dot(const DotArgs& d, double (&part)[CPT],
     double t = 0.0;
     for (int sl = 0; sl < slices; ++sl) t += red[sl * C + c];
     colsum[c] = t;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    double t = colsum[c];
+    if (d.coupled) {  // one CG per RHS: the sum over its blocks, in block order
+      const int nb = d.cp.nb, c0 = (c / nb) * nb;
+      t = 0.0;
+      for (int i = 0; i < nb; ++i) t += colsum[c0 + i];
+    }
     dot_finalize_column(d, c, t);
   }
   __syncthreads();

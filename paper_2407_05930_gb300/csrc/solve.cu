@@ -1001,7 +1001,10 @@ void amgr_apply(const Ctx& c, const void* y, void* z) {
   smooth(W.ar, 1.0);  // postsmoothing
 }
 
-// The preconditioner step of the PCG: z = M r with <r, z> (dot `d`).
+// The preconditioner step of the PCG: z = M r with <r, z> (dot `d`).  AMGR
+// is not block diagonal in the transformed basis (the AMG of A_c over the
+// full coarse domain does not keep the mirror symmetry), so with it the PCG
+// is one CG per RHS over all its blocks (DotArgs::coupled).
 static void precondition(const Ctx& c, const void* r, void* z, const DotArgs* d) {
   if (c.pc == AMGSYM_PC_AMGR) {
     amgr_apply(c, r, z);
@@ -1033,6 +1036,7 @@ static void pcg_iteration(const Ctx& c, PrecWork& W, const DevScalars& sc, int32
   Device* D = c.D;
   const ValType kmt = c.vt == VEC_F64 ? VAL_F64 : VAL_F32;  // reduced operator precision
   DotArgs dpq = make_dot(sc, DOT_WY, FIN_ALPHA, W.p, nrhs, D->nb, tol, 0);
+  dpq.coupled = c.pc == AMGSYM_PC_AMGR;
   spmm(c, D->Ainn, kmt, c.vt, c.vt, W.p, W.q, 1.0, 0.0, nullptr, true, &dpq);
   DotArgs drr = make_dot(sc, DOT_YY, FIN_CONV, nullptr, nrhs, D->nb, tol, 1);
   {
@@ -1044,6 +1048,7 @@ static void pcg_iteration(const Ctx& c, PrecWork& W, const DevScalars& sc, int32
              6 * xsize(c.vt) * D->n_b * c.C);
   }
   DotArgs drz = make_dot(sc, DOT_WY, FIN_BETA, W.r, nrhs, D->nb, tol, 0);
+  drz.coupled = c.pc == AMGSYM_PC_AMGR;
   precondition(c, W.r, W.z, &drz);
   {
     ProfScope ps(c.st);
@@ -1078,6 +1083,7 @@ static int pcg_loop(const Ctx& c0, PrecWork& W, const DevScalars& sc, int32_t nr
   graph_key.tiles_gen = D->tiles_gen;
   // start: z = M r, rz, p = z
   DotArgs drz = make_dot(sc, DOT_WY, FIN_STORE_RZ, W.r, nrhs, D->nb, tol, 0);
+  drz.coupled = c.pc == AMGSYM_PC_AMGR;
   precondition(c, W.r, W.z, &drz);
   launch_copy(c.vt, D->n_b * c.C, W.p, W.z, c.st);
   check_launch();
