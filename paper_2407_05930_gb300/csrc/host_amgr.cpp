@@ -10,9 +10,10 @@
 // inner block K-bar = I (x) K and the prolongation P = I (x) P_b with
 // P_b = [W; I] (eq. "amgreduction") are the same for every copy: in the
 // transformed basis of Alg. 1 they act on all 2^s blocks at once (SpMM).
-// W is extended+i interpolation (the paper's best choice for k = 2 is
-// DPLS + energy minimisation; extended+i is the one it names as effective at
-// k = 2, and the one this library has).
+// W is extended+i interpolation.  The paper's best configuration is k = 2
+// with DPLS + energy minimisation; with extended+i, k = 1 converges as the
+// paper's AMGR does (9-11 PCG iterations on the 32^3 model problem, s >= 1)
+// and k = 2 does not (22-26), so k = 1 is the default.
 //
 // The top-level smoother is the block FSAI of eq. "topsmoother": the FSAI of
 // K on the fine points (shared by every copy) and an FSAI of C-bar on the

@@ -64,7 +64,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->fsai_max_lower_coarse = 1;
   o->halo_kb = 0;
   o->amgr = 0;
-  o->amgr_distance = 2;
+  o->amgr_distance = 1;
   o->amgr_interp_max = 4;
 }
 

@@ -44,7 +44,8 @@ def _strength(A, theta=0.25):
     return sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=A.shape)
 
 
-@pytest.mark.parametrize("N,s,bc,k", [((16, 12, 10), 1, "dirichlet", 2), ((12, 12, 8), 2, "neumann", 2),
+@pytest.mark.parametrize("N,s,bc,k", [((16, 12, 10), 1, "dirichlet", 1), ((12, 12, 8), 2, "neumann", 1),
+                                      ((16, 12, 10), 1, "dirichlet", 2), ((12, 12, 8), 2, "neumann", 2),
                                       ((12, 8, 8), 3, "dirichlet", 2), ((14, 10, 8), 1, "dirichlet", 3)])
 def test_populated_coarsening_prolongation_and_reduced_operator(N, s, bc, k):
     g = gaussian_logk(N, s, seed=31, corr=2.0)
