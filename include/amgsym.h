@@ -324,6 +324,32 @@ amgsym_status amgsym_solve_gmres(amgsym_t h, const double* b_dev, double* x_dev,
                                  const amgsym_solve_opts* sopts, int32_t restart, int32_t use_lrc,
                                  void* stream, amgsym_solve_info* info);
 
+/* ------------------------------------------------------------------------
+ * LRCFSAI(k) (Sec. 2.1, Thm. "correction", eqs. "Ydef", "LRC", "LRCFSAI";
+ * the paper's Table "lrcfsai" runs PCG with it).
+ *
+ * amgsym_lrcfsai_setup: for every block i, the k eigenpairs of the smallest
+ * eigenvalues lambda_t of X_i = G_inn A^_i G_inn^T, where G_inn is the FSAI
+ * factor of A_inn of the setup's finest level (G_inn^T G_inn ~ A_inn^{-1}),
+ * by `steps` Lanczos steps (Euclidean inner product, full
+ * reorthogonalisation, start vector uniform[-1, 1] from `seed`), all blocks at
+ * once.  Stores Z = G_inn^T V_k and Theta Z with Theta_t = (1 - lambda_t) /
+ * lambda_t on the device; k = 0 removes the correction.  Needs a hierarchy of
+ * two levels or more with FP64 values.  Synchronises the stream.
+ * amgsym_lrcfsai_values: Ritz values (host [2^s][k]) and k, as
+ * amgsym_lrc_values.
+ *
+ * amgsym_solve_fsai: x = A^{-1} b like amgsym_solve, by PCG on the reduced
+ * system preconditioned by I (x) G_inn^T G_inn (use_lrc = 0: LRCFSAI(0)) or by
+ * eq. "LRCFSAI" (use_lrc = 1), FP64, one CG per column (the preconditioner is
+ * block diagonal), recurrence residual confirmed by the true residual.
+ * ---------------------------------------------------------------------- */
+amgsym_status amgsym_lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, void* stream);
+int32_t amgsym_lrcfsai_values(amgsym_t h, double* theta);
+amgsym_status amgsym_solve_fsai(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                                const amgsym_solve_opts* sopts, int32_t use_lrc, void* stream,
+                                amgsym_solve_info* info);
+
 /* Adjoint solve A^T lambda = g.  A is symmetric, so this is the same reduced
  * solve; kept as its own entry point for the differentiable interface. */
 amgsym_status amgsym_solve_adjoint(amgsym_t h, const double* g_dev, double* lam_dev,

@@ -12,7 +12,12 @@ Dense linear algebra on small matrices, written from the statements:
   sum runs over the nonzero part of the spectrum of ``Y``;
 * ``low_rank_corrected(A, Binv, k)``: the rank-k truncation of eq.
   "LRC_AMG", keeping the k smallest eigenvalues ``lambda`` of
-  ``X = Binv A`` (``Sigma = I - Lambda``, ``Theta = (Sigma^{-1} - I)^{-1}``).
+  ``X = Binv A`` (``Sigma = I - Lambda``, ``Theta = (Sigma^{-1} - I)^{-1}``);
+* ``factored_corrected(A, G, k)``: Thm. "correction" and eq. "LRC" for a
+  factored approximate inverse ``G^T G``: with ``Y = I - G A G^T = V Sigma
+  V^T``, ``A^{-1} = G^T G + G^T V Sigma (I - Sigma)^{-1} V^T G``; ``k = None``
+  keeps every eigenpair (the exact inverse), else the k of the smallest
+  eigenvalues of ``G A G^T``.
 """
 
 from __future__ import annotations
@@ -55,3 +60,19 @@ def low_rank_corrected(A: np.ndarray, Binv: np.ndarray, k: int):
     lam_k, U_k, V_k = lam[:k], U[:, :k], V[:, :k]
     theta = (1.0 - lam_k) / lam_k  # (Sigma^{-1} - I)^{-1} with Sigma = I - Lambda
     return (np.eye(n) + U_k @ np.diag(theta) @ V_k.T) @ Binv, lam_k
+
+
+def factored_corrected(A: np.ndarray, G: np.ndarray, k=None):
+    """(M, lam): G^T G + Z Theta Z^T with Z = G^T V (eqs. "LRC", "LRCFSAI") and
+    the eigenvalues lam of G A G^T it corrects (all of them for k = None)."""
+    X = G @ A @ G.T
+    X = 0.5 * (X + X.T)
+    lam, V = np.linalg.eigh(X)
+    if k is not None:
+        lam, V = lam[:k], V[:, :k]
+    sigma = 1.0 - lam
+    keep = np.abs(1.0 - sigma) > 0.0  # lambda != 0
+    theta = np.zeros_like(sigma)
+    theta[keep] = sigma[keep] / (1.0 - sigma[keep])
+    Z = G.T @ V
+    return G.T @ G + Z @ np.diag(theta) @ Z.T, lam

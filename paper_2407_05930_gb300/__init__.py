@@ -153,6 +153,9 @@ def _load():
         "amgsym_is_singular": (i32, [P]),
         "amgsym_lrc_setup": (i32, [P, i32, i32, ctypes.c_uint64, P]),
         "amgsym_amgr_apply": (i32, [P, P, P, i32, i32, P]),
+        "amgsym_lrcfsai_setup": (i32, [P, i32, i32, ctypes.c_uint64, P]),
+        "amgsym_lrcfsai_values": (i32, [P, pdbl]),
+        "amgsym_solve_fsai": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), i32, P, ctypes.POINTER(SolveInfo)]),
         "amgsym_amgr_info": (i32, [P, pi64, pi64, pi64, pi32, ctypes.POINTER(ctypes.c_int8)]),
         "amgsym_amgr_matrix": (i32, [P, i32, pi64, pi32, pdbl]),
         "amgsym_lrc_values": (i32, [P, pdbl]),
@@ -190,7 +193,7 @@ EXPORTED = [
         "amgsym_batch_create amgsym_batch_solve amgsym_batch_destroy amgsym_get_tiles amgsym_level_dia "
         "amgsym_cycle_timeout_check amgsym_profile_step amgsym_fv_assemble_bc amgsym_is_singular "
         "amgsym_lrc_setup amgsym_lrc_values amgsym_solve_gmres amgsym_amgr_apply amgsym_amgr_info "
-        "amgsym_amgr_matrix"
+        "amgsym_amgr_matrix amgsym_lrcfsai_setup amgsym_lrcfsai_values amgsym_solve_fsai"
     ).split()
 ]
 
@@ -474,6 +477,40 @@ class Problem:
         out = np.empty(self.nb * k, dtype=np.float64)
         lib.amgsym_lrc_values(self._h, _ptr(out, ctypes.c_double))
         return out.reshape(self.nb, k)
+
+    def lrcfsai_setup(self, k: int, steps: int = 60, seed: int = 7):
+        """LRCFSAI(k): the k smallest eigenpairs of G_inn A^_i G_inn^T per block."""
+        _check(lib.amgsym_lrcfsai_setup(self._h, int(k), int(steps), int(seed), self._stream()))
+        return self
+
+    def lrcfsai_values(self) -> np.ndarray:
+        k = lib.amgsym_lrcfsai_values(self._h, None)
+        if k <= 0:
+            return np.zeros((self.nb, 0))
+        out = np.empty(self.nb * k, dtype=np.float64)
+        lib.amgsym_lrcfsai_values(self._h, _ptr(out, ctypes.c_double))
+        return out.reshape(self.nb, k)
+
+    def solve_fsai(self, b, x=None, lrc: bool = False, **kw) -> SolveResult:
+        """PCG with I (x) G_inn^T G_inn, optionally LRCFSAI-corrected (amgsym_solve_fsai); FP64."""
+        import torch
+
+        if not (isinstance(b, torch.Tensor) and b.is_cuda and b.dtype == torch.float64):
+            raise TypeError("b must be a CUDA float64 tensor")
+        bb = b.reshape(-1, self.n).contiguous()
+        nrhs = bb.shape[0]
+        if x is None:
+            x = torch.empty_like(bb)
+        xx = x.reshape(-1, self.n)
+        o = default_solve_opts(**kw)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        info = SolveInfo()
+        info.relres = _ptr(rel, ctypes.c_double)
+        code = lib.amgsym_solve_fsai(self._h, ctypes.c_void_p(bb.data_ptr()), ctypes.c_void_p(xx.data_ptr()), nrhs,
+                                     self.n, ctypes.byref(o), 1 if lrc else 0, self._stream(), ctypes.byref(info))
+        _check(code)
+        res = SolveResult(info.iters, info.outer_iters, bool(info.converged), rel, STATUS[code])
+        return (x if x.shape == b.shape else xx.reshape(b.shape)), res
 
     def solve_gmres(self, b, x=None, restart: int = 30, lrc: bool = False, **kw) -> SolveResult:
         """Restarted GMRES with the LRCAMG preconditioner (amgsym_solve_gmres); FP64."""

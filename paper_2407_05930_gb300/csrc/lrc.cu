@@ -380,6 +380,247 @@ static amgsym_status gmres_impl(amgsym_t h, const double* b_dev, double* x_dev, 
   return converged ? AMGSYM_OK : AMGSYM_NOT_CONVERGED;
 }
 
+// ---------------------------------------------------------------------------
+// LRCFSAI(k) (Sec. 2.1, Thm. "correction", eqs. "Ydef", "LRC", "LRCFSAI"):
+// the FSAI of A_inn, G_inn^T G_inn ~ A_inn^{-1}, corrected per block.  With
+// X = G_inn A^_i G_inn^T (symmetric) and its k eigenpairs of the smallest
+// eigenvalues (V_k, Lambda_k), Y = I - X has Sigma = I - Lambda and the
+// correction is Z_k Theta_k Z_k^T with Z_k = G_inn^T V_k and
+// Theta = Sigma (I - Sigma)^{-1}: Theta_t = (1 - lambda_t) / lambda_t.  The
+// pairs come from Lanczos on X (Euclidean inner product, full
+// reorthogonalisation) for all blocks at once; the preconditioner is
+// symmetric, so the solve is PCG.
+
+static void lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, cudaStream_t st) {
+  Device* D = require_dev(h);
+  D->lrcf_k = 0;
+  D->lrcf_Z = D->lrcf_TZ = nullptr;
+  D->lrcf_theta.clear();
+  if (k == 0) return;
+  const DevLevel& L = D->lv[0];
+  if (L.cinv || !L.G.v64 || !L.Gt.v64)
+    fail(AMGSYM_ERR_STATE, "LRCFSAI needs the FP64 FSAI factor of A_inn (a hierarchy of two levels or more, "
+                           "opts.precisions with FP64)");
+  const int32_t nb = D->nb, C = nb;
+  const int64_t n_b = D->n_b, len = n_b * C;
+  const int m = steps;
+  ensure_work(D, 1, VEC_F64);
+  Ctx c{D, C, VEC_F64, VAL_F64, false, st};
+  PrecWork& W = D->w64;
+  DevBuf Q((int64_t)(m + 1) * len), w(len), part((int64_t)mdot_blocks(n_b, C) * (m + 1) * C), Hd((int64_t)(m + 1) * C),
+      sd(C);
+  {
+    std::vector<double> q0((size_t)len);
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U(-1.0, 1.0);
+    for (auto& v : q0) v = U(rng);
+    to_dev(Q.p, q0.data(), len, st);
+  }
+  std::vector<double> hh((size_t)(m + 1) * C), sv(C);
+  auto normalise = [&](double* q) {  // q /= ||q|| per column; returns ||q||^2
+    launch_mdot(q, 0, C, 1, q, n_b, C, part.p, Hd.p, st);
+    check_launch();
+    to_host(hh.data(), Hd.p, C, st);
+    for (int j = 0; j < C; ++j) sv[j] = hh[j] > 0.0 ? 1.0 / std::sqrt(hh[j]) : 0.0;
+    to_dev(sd.p, sv.data(), C, st);
+    launch_colscale(q, sd.p, q, n_b, C, st);
+    check_launch();
+    return std::vector<double>(hh.begin(), hh.begin() + C);
+  };
+  auto apply_X = [&](const double* q, double* out) {  // out = G A^ G^T q
+    spmm(c, L.Gt, VAL_F64, VEC_F64, VEC_F64, q, W.z, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, D->Ainn, VAL_F64, VEC_F64, VEC_F64, W.z, W.q, 1.0, 0.0, nullptr, true, nullptr);
+    spmm(c, L.G, VAL_F64, VEC_F64, VEC_F64, W.q, out, 1.0, 0.0, nullptr, false, nullptr);
+  };
+  normalise(Q.p);
+  std::vector<double> alpha((size_t)m * C, 0.0), beta((size_t)m * C, 0.0);
+  std::vector<int> mc(C, m);
+  for (int j = 0; j < m; ++j) {
+    apply_X(Q.p + (int64_t)j * len, w.p);
+    std::vector<double> h_sum((size_t)(j + 1) * C, 0.0);
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_mdot(Q.p, len, C, j + 1, w.p, n_b, C, part.p, Hd.p, st);
+      launch_maxpy(Q.p, len, C, j + 1, Hd.p, -1.0, w.p, n_b, C, st);
+      check_launch();
+      to_host(hh.data(), Hd.p, (int64_t)(j + 1) * C, st);
+      for (int64_t t = 0; t < (int64_t)(j + 1) * C; ++t) h_sum[t] += hh[t];
+    }
+    for (int col = 0; col < C; ++col) alpha[(size_t)j * C + col] = h_sum[(size_t)j * C + col];
+    double* qn = Q.p + (int64_t)(j + 1) * len;
+    CK(cudaMemcpyAsync(qn, w.p, sizeof(double) * (size_t)len, cudaMemcpyDeviceToDevice, st));
+    const std::vector<double> b2 = normalise(qn);
+    for (int col = 0; col < C; ++col) {
+      double amax = 0.0;
+      for (int i = 0; i <= j; ++i) amax = std::max(amax, std::fabs(alpha[(size_t)i * C + col]));
+      const double b = b2[col] > 0.0 ? std::sqrt(b2[col]) : 0.0;
+      beta[(size_t)j * C + col] = b;
+      if (mc[col] == m && !(b > 1e-10 * amax)) mc[col] = j + 1;
+    }
+  }
+  std::vector<double> theta((size_t)C * k, 0.0), Y((size_t)m * k * C, 0.0);
+  std::vector<double> Th((size_t)k * C, 0.0);
+  for (int col = 0; col < C; ++col) {
+    const int mm = mc[col];
+    std::vector<double> T((size_t)mm * mm, 0.0), V;
+    for (int i = 0; i < mm; ++i) {
+      T[(size_t)i * mm + i] = alpha[(size_t)i * C + col];
+      if (i + 1 < mm) T[(size_t)i * mm + i + 1] = T[(size_t)(i + 1) * mm + i] = beta[(size_t)i * C + col];
+    }
+    jacobi_eig(T, V, mm);
+    std::vector<int> order(mm);
+    for (int i = 0; i < mm; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return T[(size_t)a * mm + a] < T[(size_t)b * mm + b]; });
+    for (int t = 0; t < k && t < mm; ++t) {
+      const int e = order[t];
+      const double th = T[(size_t)e * mm + e];
+      theta[(size_t)col * k + t] = th;
+      Th[(size_t)t * C + col] = th > 0.0 ? (1.0 - th) / th : 0.0;  // Sigma (I - Sigma)^{-1}
+      for (int i = 0; i < mm; ++i) Y[((size_t)t * m + i) * C + col] = V[(size_t)i * mm + e];
+    }
+  }
+  // Z_t = G^T (Q Y_t), Theta Z_t
+  double* Z = nullptr;
+  double* TZ = nullptr;
+  CK(cudaMalloc(&Z, sizeof(double) * (size_t)k * len));
+  D->owned.push_back(Z);
+  CK(cudaMalloc(&TZ, sizeof(double) * (size_t)k * len));
+  D->owned.push_back(TZ);
+  for (int t = 0; t < k; ++t) {
+    CK(cudaMemsetAsync(w.p, 0, sizeof(double) * (size_t)len, st));
+    to_dev(Hd.p, Y.data() + (size_t)t * m * C, (int64_t)m * C, st);
+    launch_maxpy(Q.p, len, C, m, Hd.p, 1.0, w.p, n_b, C, st);
+    spmm(c, L.Gt, VAL_F64, VEC_F64, VEC_F64, w.p, Z + (int64_t)t * len, 1.0, 0.0, nullptr, false, nullptr);
+    to_dev(sd.p, Th.data() + (size_t)t * C, C, st);
+    launch_colscale(Z + (int64_t)t * len, sd.p, TZ + (int64_t)t * len, n_b, C, st);
+    check_launch();
+  }
+  CK(cudaStreamSynchronize(st));
+  D->lrcf_k = k;
+  D->lrcf_Z = Z;
+  D->lrcf_TZ = TZ;
+  D->lrcf_theta = theta;
+}
+
+// PCG on the reduced system with I (x) G_inn^T G_inn (+ the LRCFSAI correction),
+// FP64, one CG per column (the preconditioner is block diagonal).
+static amgsym_status fsai_pcg_impl(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                                   const amgsym_solve_opts* sopts, int32_t use_lrc, cudaStream_t st,
+                                   amgsym_solve_info* info) {
+  Device* D = require_dev(h);
+  amgsym_solve_opts o;
+  amgsym_solve_opts_default(&o);
+  if (sopts) o = *sopts;
+  if (nrhs < 1 || (int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
+  if (ld < h->n || !b_dev || !x_dev) fail(AMGSYM_ERR_ARG, "bad vectors or ld");
+  if (o.precision != AMGSYM_PREC_FP64) fail(AMGSYM_ERR_ARG, "the FSAI-preconditioned solve runs in FP64");
+  if (!(o.tol > 0.0) || o.maxit < 1) fail(AMGSYM_ERR_ARG, "bad tolerance or maxit");
+  const DevLevel& L = D->lv[0];
+  if (L.cinv || !L.G.v64 || !L.Gt.v64) fail(AMGSYM_ERR_STATE, "no FP64 FSAI factor of A_inn");
+  if (use_lrc && D->lrcf_k <= 0) fail(AMGSYM_ERR_STATE, "no LRCFSAI correction: call amgsym_lrcfsai_setup first");
+  ensure_work(D, nrhs, VEC_F64);
+  const int32_t nb = D->nb, C = nrhs * nb;
+  const int64_t n_b = D->n_b, len = n_b * C;
+  Ctx c{D, C, VEC_F64, VAL_F64, false, st};
+  PrecWork& W = D->w64;  // r, z, p, q; x^ in D->xh
+  DevBuf t(len), part((int64_t)mdot_blocks(n_b, C) * std::max(2, D->lrcf_k + 1) * C), Hd((int64_t)std::max(2, D->lrcf_k) * C),
+      sd(C);
+  double* bh = D->bh;
+  double* xh = D->xh;
+  launch_transform_fwd(b_dev, nrhs, ld, D->perm, n_b, D->s, bh, VEC_F64, st);
+  check_launch();
+  if (D->singular) launch_sub_block0_mean(bh, n_b, nrhs, nb, D->sc_out.partials, D->sc_out.partial_cap, st);
+  if (o.use_x0)
+    launch_transform_fwd(x_dev, nrhs, ld, D->perm, n_b, D->s, xh, VEC_F64, st);
+  else
+    CK(cudaMemsetAsync(xh, 0, sizeof(double) * (size_t)len, st));
+  check_launch();
+  double* r = static_cast<double*>(W.r);
+  double* z = static_cast<double*>(W.z);
+  double* p = static_cast<double*>(W.p);
+  double* q = static_cast<double*>(W.q);
+  std::vector<double> hv(C), bn2(nrhs, 0.0), rz(C), sv(C), ones(C, 1.0);
+  auto coldot = [&](const double* a, const double* b, std::vector<double>& out) {
+    launch_mdot(a, 0, C, 1, b, n_b, C, part.p, Hd.p, st);
+    check_launch();
+    to_host(out.data(), Hd.p, C, st);
+  };
+  auto precond = [&](const double* rr, double* zz) {  // zz = G^T G rr (+ Z Theta Z^T rr)
+    spmm(c, L.G, VAL_F64, VEC_F64, VEC_F64, rr, t.p, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, L.Gt, VAL_F64, VEC_F64, VEC_F64, t.p, zz, 1.0, 0.0, nullptr, false, nullptr);
+    if (use_lrc) {
+      const int64_t vs = n_b * nb;
+      launch_mdot(D->lrcf_TZ, vs, nb, D->lrcf_k, rr, n_b, C, part.p, Hd.p, st);
+      launch_maxpy(D->lrcf_Z, vs, nb, D->lrcf_k, Hd.p, 1.0, zz, n_b, C, st);
+      check_launch();
+    }
+  };
+  auto relres = [&](const std::vector<double>& col2, std::vector<double>& rel) {
+    rel.assign(nrhs, 0.0);
+    for (int col = 0; col < C; ++col) rel[col / nb] += col2[col];
+    bool ok = true;
+    for (int rr = 0; rr < nrhs; ++rr) {
+      rel[rr] = bn2[rr] > 0.0 ? std::sqrt(rel[rr] / bn2[rr]) : 0.0;
+      if (!(rel[rr] <= o.tol)) ok = false;
+    }
+    return ok;
+  };
+  coldot(bh, bh, hv);
+  for (int col = 0; col < C; ++col) bn2[col / nb] += hv[col];
+  std::vector<double> rel;
+  int it = 0;
+  bool converged = false;
+  for (int restart = 0; restart < 3 && !converged && it < o.maxit; ++restart) {
+    spmm(c, D->Ainn, VAL_F64, VEC_F64, VEC_F64, xh, r, -1.0, 1.0, bh, true, nullptr);  // r = b^ - A^ x^
+    coldot(r, r, hv);
+    if (relres(hv, rel)) {
+      converged = true;
+      break;
+    }
+    precond(r, z);
+    CK(cudaMemcpyAsync(p, z, sizeof(double) * (size_t)len, cudaMemcpyDeviceToDevice, st));
+    coldot(r, z, rz);
+    for (; it < o.maxit; ++it) {
+      spmm(c, D->Ainn, VAL_F64, VEC_F64, VEC_F64, p, q, 1.0, 0.0, nullptr, true, nullptr);  // q = A^ p
+      coldot(p, q, hv);
+      for (int col = 0; col < C; ++col) sv[col] = hv[col] > 0.0 ? rz[col] / hv[col] : 0.0;  // alpha
+      to_dev(Hd.p, sv.data(), C, st);
+      launch_maxpy(p, 0, C, 1, Hd.p, 1.0, xh, n_b, C, st);   // x += alpha p
+      launch_maxpy(q, 0, C, 1, Hd.p, -1.0, r, n_b, C, st);   // r -= alpha q
+      check_launch();
+      coldot(r, r, hv);
+      if (relres(hv, rel)) {
+        ++it;
+        break;
+      }
+      precond(r, z);
+      std::vector<double> rz_new(C);
+      coldot(r, z, rz_new);
+      for (int col = 0; col < C; ++col) sv[col] = rz[col] != 0.0 ? rz_new[col] / rz[col] : 0.0;  // beta
+      rz = rz_new;
+      to_dev(sd.p, sv.data(), C, st);
+      launch_colscale(p, sd.p, p, n_b, C, st);                 // p = beta p
+      to_dev(Hd.p, ones.data(), C, st);
+      launch_maxpy(z, 0, C, 1, Hd.p, 1.0, p, n_b, C, st);      // p += z
+      check_launch();
+    }
+    // confirm with the true residual
+    spmm(c, D->Ainn, VAL_F64, VEC_F64, VEC_F64, xh, r, -1.0, 1.0, bh, true, nullptr);
+    coldot(r, r, hv);
+    converged = relres(hv, rel);
+  }
+  if (D->singular) launch_sub_block0_mean(xh, n_b, nrhs, nb, D->sc_out.partials, D->sc_out.partial_cap, st);
+  launch_transform_bwd(xh, VEC_F64, nrhs, D->perm, n_b, D->s, x_dev, ld, st);
+  check_launch();
+  CK(cudaStreamSynchronize(st));
+  if (info) {
+    info->iters = it;
+    info->outer_iters = 0;
+    info->converged = converged ? 1 : 0;
+    if (info->relres) std::memcpy(info->relres, rel.data(), sizeof(double) * nrhs);
+  }
+  return converged ? AMGSYM_OK : AMGSYM_NOT_CONVERGED;
+}
+
 }  // namespace amgsym
 
 using namespace amgsym;
@@ -412,6 +653,43 @@ extern "C" amgsym_status amgsym_solve_gmres(amgsym_t h, const double* b_dev, dou
                                             void* stream, amgsym_solve_info* info) {
   try {
     return gmres_impl(h, b_dev, x_dev, nrhs, ld, sopts, restart, use_lrc, static_cast<cudaStream_t>(stream), info);
+  } catch (const amgsym::Error& e) {
+    amgsym::set_last_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    amgsym::set_last_error("host allocation failed");
+    return AMGSYM_ERR_OOM;
+  }
+}
+
+extern "C" amgsym_status amgsym_lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, void* stream) {
+  try {
+    if (!h) fail(AMGSYM_ERR_ARG, "NULL handle");
+    if (k < 0 || k > 64) fail(AMGSYM_ERR_ARG, "k must be in [0, 64]");
+    if (k > 0 && (steps < k || steps > 400)) fail(AMGSYM_ERR_ARG, "steps must be in [k, 400]");
+    lrcfsai_setup(h, k, steps, seed, static_cast<cudaStream_t>(stream));
+    return AMGSYM_OK;
+  } catch (const amgsym::Error& e) {
+    amgsym::set_last_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    amgsym::set_last_error("host allocation failed");
+    return AMGSYM_ERR_OOM;
+  }
+}
+
+extern "C" int32_t amgsym_lrcfsai_values(amgsym_t h, double* theta) {
+  if (!h || !h->dev) return -1;
+  Device* D = h->dev;
+  if (theta && D->lrcf_k > 0) std::memcpy(theta, D->lrcf_theta.data(), sizeof(double) * D->lrcf_theta.size());
+  return D->lrcf_k;
+}
+
+extern "C" amgsym_status amgsym_solve_fsai(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
+                                           const amgsym_solve_opts* sopts, int32_t use_lrc, void* stream,
+                                           amgsym_solve_info* info) {
+  try {
+    return fsai_pcg_impl(h, b_dev, x_dev, nrhs, ld, sopts, use_lrc, static_cast<cudaStream_t>(stream), info);
   } catch (const amgsym::Error& e) {
     amgsym::set_last_error(e.msg);
     return e.code;

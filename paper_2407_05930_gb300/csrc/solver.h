@@ -141,6 +141,13 @@ struct Device {
   std::vector<double> lrc_theta;
   bool has_amgr = false;
   DevAmgr amgr;
+  // Low-rank correction of LRCFSAI(k) (eq. "LRCFSAI"), per block: Z = G_inn^T V
+  // (V the k eigenvectors of G_inn A^_i G_inn^T of the smallest eigenvalues)
+  // and Theta Z, both [k][n_b][nb]; Ritz values [nb][k] (host).
+  int32_t lrcf_k = 0;
+  double* lrcf_Z = nullptr;
+  double* lrcf_TZ = nullptr;
+  std::vector<double> lrcf_theta;
 };
 
 struct Ctx {

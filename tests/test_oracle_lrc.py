@@ -74,3 +74,23 @@ def test_rank_k_correction_moves_the_smallest_eigenvalues_to_one():
     mu = np.sort(np.linalg.eigvals(P @ Ai).real)
     assert np.sum(np.abs(mu - 1.0) <= 1e-8) >= k  # the k smallest moved to 1
     assert np.allclose(mu[:-k] if k else mu, np.sort(np.concatenate([lam[k:], np.ones(k)]))[:-k], rtol=1e-8)
+
+
+def test_factored_correction_theorem():
+    """Thm. "correction" with a factored approximate inverse: all pairs give
+    A^{-1}; the rank-k correction moves the k smallest eigenvalues of the
+    preconditioned operator to 1 (eq. "LRC")."""
+    Ainn, hat = _blocks((8, 6, 4), 2)
+    L = np.linalg.cholesky(Ainn)
+    G = np.tril(np.linalg.inv(L))
+    G = np.where(np.abs(G) >= 0.05 * np.abs(G).max(axis=1, keepdims=True), G, 0.0)  # a sparse approximation
+    for Ai in hat:
+        M, _ = lrc.factored_corrected(Ai, G)
+        assert np.linalg.norm(M @ Ai - np.eye(Ai.shape[0])) <= 1e-8
+        k = 6
+        Mk, lam_k = lrc.factored_corrected(Ai, G, k)
+        mu = np.sort(np.linalg.eigvals(Mk @ Ai).real)
+        lam = np.sort(np.linalg.eigvalsh(G @ Ai @ G.T))
+        assert np.allclose(lam_k, lam[:k], rtol=1e-10)
+        assert np.sum(np.abs(mu - 1.0) <= 1e-8) >= k
+        assert np.allclose(np.sort(np.concatenate([lam[k:], np.ones(k)])), mu, rtol=1e-8, atol=1e-12)
