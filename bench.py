@@ -468,8 +468,8 @@ def run_model_tables(args):
     iteration counts of this library's solvers next to the paper's Tables
     "lrcamg" (GMRES + LRCAMG(k)) and "amgr" (PCG + AMGR), to relative
     residual 1e-8.  PCG with I (x) M_inn^{-1} (s = 0: AMG of the full
-    domain), PCG with AMGR, and GMRES(60) with LRCAMG(k), k = 0, 1, 2, 4, 8,
-    16."""
+    domain), PCG with AMGR, GMRES(60) with LRCAMG(k) and PCG with LRCFSAI(k),
+    k = 0, 1, 2, 4, 8, 16 (Table "lrcfsai")."""
     import torch
 
     import paper_2407_05930_gb300 as amg
@@ -480,7 +480,7 @@ def run_model_tables(args):
     N = (args.model_grid,) * 3
     h = grid.widths(N, 1.5)
     ks = (0, 1, 2, 4, 8, 16)
-    pcg, gm, amgr, relmax = {}, {}, {}, 0.0
+    pcg, gm, amgr, fs, relmax = {}, {}, {}, {}, 0.0
     for s in range(4):
         P = amg.Problem.structured(N, 1.5, None, s, bc="neumann").setup(amgr=1)
         f = np.random.default_rng(94).uniform(-1.0, 1.0, P.n)
@@ -500,13 +500,26 @@ def run_model_tables(args):
             row.append(info.iters if info.converged else None)
             relmax = max(relmax, float(np.max(info.relres)))
         gm[s] = row
+        row = []
+        for k in ks:
+            if k:
+                P.lrcfsai_setup(k, steps=max(60, 4 * k))
+            x, info = P.solve_fsai(bt, lrc=k > 0, tol=1e-8, maxit=5000)
+            row.append(info.iters if info.converged else None)
+            relmax = max(relmax, float(np.max(info.relres)))
+        fs[s] = row
         P.close()
     line = {"workload": f"neumann model problem {N[0]}^3, tanh 1.5, s = 0..3, relres 1e-8",
             "pcg_I_x_Minn": pcg, "pcg_amgr": amgr, "gmres_lrcamg": {"k": list(ks), "iters_by_s": gm},
+            "pcg_lrcfsai": {"k": list(ks), "iters_by_s": fs},
             "max_relres": relmax,
             "paper_64cube": {"gmres_AMG": [6, 6, 6, 6], "gmres_LRCAMG": {"0": [6, 23, 29, 29], "1": [9, 23, 26, 24],
                              "2": [9, 23, 22, 24], "4": [9, 19, 21, 20], "8": [9, 17, 18, 18],
-                             "16": [9, 15, 16, 15]}, "pcg_AMGR": [6, 9, 9, 9]}}
+                             "16": [9, 15, 16, 15]}, "pcg_AMGR": [6, 9, 9, 9],
+                             "pcg_LRCFSAI": {"FSAI": [291, 220, 173, 121], "0": [291, 241, 193, 149],
+                                             "1": [228, 194, 146, 106], "2": [228, 172, 124, 92],
+                                             "4": [186, 136, 107, 83], "8": [131, 111, 81, 61],
+                                             "16": [113, 82, 63, 50]}}}
     print(json.dumps(line), flush=True)
 
 
