@@ -25,7 +25,27 @@ __device__ __forceinline__ void coarse_rows_warp(int32_t n, int32_t C, const dou
       double acc[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-      for (int j = lane; j < n; j += 32) {
+      // four terms per lane in flight (all loads first, then the fmas in
+      // ascending j: the same sum as one term at a time)
+      int j = lane;
+      for (; j + 96 < n; j += 128) {
+        double av[4];
+        double yv[4][8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          av[u] = a[j + 32 * u];
+          const T* y = Y + (int64_t)(j + 32 * u) * C + c0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) yv[u][q] = q < nc ? (double)ld(y + q) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (q < nc) acc[q] = fma(av[u], yv[u][q], acc[q]);
+        }
+      }
+      for (; j < n; j += 32) {
         const double av = a[j];
         const T* y = Y + (int64_t)j * C + c0;
 #pragma unroll

@@ -35,7 +35,7 @@
 namespace amgsym {
 
 template <typename MT, typename XT, typename OT, int CPT, int KL, bool HAS_DOT, bool HAS_IFACE, bool DIA>
-__global__ void __launch_bounds__(kBlock, ((DIA || CPT >= 8) ? 4 : (HAS_DOT || HAS_IFACE) ? 6 : 8)) spmm_kernel(SpmmArgs a) {
+__global__ void __launch_bounds__(kBlock, ((DIA && HAS_DOT) ? 3 : (DIA || CPT >= 8) ? 4 : (HAS_DOT || HAS_IFACE) ? 6 : 8)) spmm_kernel(SpmmArgs a) {
   using DT = typename AccOf<XT>::type;
   if (a.skip && *a.skip == 0) return;  // uniform over the grid
   DT dpart[CPT];
