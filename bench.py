@@ -481,6 +481,7 @@ def run_model_tables(args):
     h = grid.widths(N, 1.5)
     ks = (0, 1, 2, 4, 8, 16)
     pcg, gm, amgr, fs, relmax = {}, {}, {}, {}, 0.0
+    gm_setup, fs_setup = {}, {}
     for s in range(4):
         P = amg.Problem.structured(N, 1.5, None, s, bc="neumann").setup(amgr=1)
         f = np.random.default_rng(94).uniform(-1.0, 1.0, P.n)
@@ -493,25 +494,29 @@ def run_model_tables(args):
         x, info = P.solve(bt, tol=1e-8, preconditioner=amg.PC_AMGR)
         amgr[s] = info.iters
         relmax = max(relmax, float(np.max(info.relres)))
-        row = []
+        row, srow = [], []
         for k in ks:
-            P.lrc_setup(k, steps=max(40, 3 * k))
+            t0 = time.perf_counter()
+            P.lrc_setup(k)
+            srow.append(round(time.perf_counter() - t0, 3))
             x, info = P.solve_gmres(bt, restart=60, lrc=k > 0, tol=1e-8, maxit=400)
             row.append(info.iters if info.converged else None)
             relmax = max(relmax, float(np.max(info.relres)))
-        gm[s] = row
-        row = []
+        gm[s], gm_setup[s] = row, srow
+        row, srow = [], []
         for k in ks:
+            t0 = time.perf_counter()
             if k:
-                P.lrcfsai_setup(k, steps=max(60, 4 * k))
+                P.lrcfsai_setup(k)
+            srow.append(round(time.perf_counter() - t0, 3))
             x, info = P.solve_fsai(bt, lrc=k > 0, tol=1e-8, maxit=5000)
             row.append(info.iters if info.converged else None)
             relmax = max(relmax, float(np.max(info.relres)))
-        fs[s] = row
+        fs[s], fs_setup[s] = row, srow
         P.close()
     line = {"workload": f"neumann model problem {N[0]}^3, tanh 1.5, s = 0..3, relres 1e-8",
-            "pcg_I_x_Minn": pcg, "pcg_amgr": amgr, "gmres_lrcamg": {"k": list(ks), "iters_by_s": gm},
-            "pcg_lrcfsai": {"k": list(ks), "iters_by_s": fs},
+            "pcg_I_x_Minn": pcg, "pcg_amgr": amgr, "gmres_lrcamg": {"k": list(ks), "iters_by_s": gm, "setup_s_by_s": gm_setup},
+            "pcg_lrcfsai": {"k": list(ks), "iters_by_s": fs, "setup_s_by_s": fs_setup},
             "max_relres": relmax,
             "paper_64cube": {"gmres_AMG": [6, 6, 6, 6], "gmres_LRCAMG": {"0": [6, 23, 29, 29], "1": [9, 23, 26, 24],
                              "2": [9, 23, 22, 24], "4": [9, 19, 21, 20], "8": [9, 17, 18, 18],

@@ -292,16 +292,29 @@ amgsym_status amgsym_solve(amgsym_t h, const double* b_dev, double* x_dev, int32
  * "LRC_AMG", "LRCAMG"; the paper's Table "lrcamg" runs GMRES with it).
  *
  * amgsym_lrc_setup: for every block i, the k eigenpairs (lambda_t, u_t) of
- * X_i = M_inn^{-1} A^_i with the smallest eigenvalues, by `steps` steps of
- * Lanczos in the A^_i inner product (full reorthogonalisation; start vector
- * uniform[-1, 1] from `seed`), all blocks at once on the device.  The Ritz
+ * X_i = M_inn^{-1} A^_i with the smallest eigenvalues, by Lanczos in the
+ * A^_i inner product, all blocks at once on the device.  The search (the
+ * "eigenpair search" below) keeps a basis of `steps` vectors.  The Ritz
  * vectors u_t are A^_i-orthonormal, so v_t = A^_i u_t are the left
  * eigenvectors with V^T U = I, and the correction of eq. "LRC_AMG" is
  * (I + U Theta V^T) M_inn^{-1} with Theta_t = (1 - lambda_t) / lambda_t: it
  * maps those eigenvalues of the preconditioned block to 1.  Stores U and
  * Theta V on the device (2 k n values per block set); k = 0 removes the
- * correction.  k in [0, 64], steps in [k, 400].  Needs amgsym_setup; a new
- * setup discards the correction.  Synchronises the stream.
+ * correction.  k in [0, 64], steps in [k + 2, 400], tol in (0, 1].  Needs
+ * amgsym_setup; a new setup discards the correction.  Synchronises the
+ * stream.
+ *
+ * Eigenpair search (both setups): thick-restarted Lanczos with full
+ * reorthogonalisation (Wu and Simon) on a basis of `steps` vectors,
+ * restarted from the max(k + 4, steps / 2) (at most steps - 2) smallest Ritz
+ * vectors, until the k smallest Ritz pairs have residual norms <= tol *
+ * lambda (at most 200 restarts); then up to 3 more such runs from new
+ * random vectors kept orthogonal to every pair found (so every copy of a
+ * multiple eigenvalue is found), stopping when a run finds nothing below the
+ * k-th smallest value so far.  Start vectors are uniform[-1, 1] from `seed`.
+ * tol = 0.1 gives the rough pairs the paper finds sufficient; small tol
+ * (1e-10) gives the eigenpairs to rounding.  A block with fewer than k
+ * pairs (a space smaller than k) keeps what it has (theta 0 past them).
  *
  * amgsym_lrc_values: copies the Ritz values (host, [2^s][k], block-major)
  * into theta (may be NULL) and returns k (0: no correction, -1: no device
@@ -318,7 +331,7 @@ amgsym_status amgsym_solve(amgsym_t h, const double* b_dev, double* x_dev, int32
  * iterations.  FP64 only (sopts->precision must be AMGSYM_PREC_FP64);
  * sopts->finest_hat applies to the V-cycle.  info->iters = GMRES iterations.
  * ---------------------------------------------------------------------- */
-amgsym_status amgsym_lrc_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, void* stream);
+amgsym_status amgsym_lrc_setup(amgsym_t h, int32_t k, int32_t steps, double tol, uint64_t seed, void* stream);
 int32_t amgsym_lrc_values(amgsym_t h, double* theta);
 amgsym_status amgsym_solve_gmres(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
                                  const amgsym_solve_opts* sopts, int32_t restart, int32_t use_lrc,
@@ -331,11 +344,13 @@ amgsym_status amgsym_solve_gmres(amgsym_t h, const double* b_dev, double* x_dev,
  * amgsym_lrcfsai_setup: for every block i, the k eigenpairs of the smallest
  * eigenvalues lambda_t of X_i = G_inn A^_i G_inn^T, where G_inn is the FSAI
  * factor of A_inn of the setup's finest level (G_inn^T G_inn ~ A_inn^{-1}),
- * by `steps` Lanczos steps (Euclidean inner product, full
- * reorthogonalisation, start vector uniform[-1, 1] from `seed`), all blocks at
- * once.  Stores Z = G_inn^T V_k and Theta Z with Theta_t = (1 - lambda_t) /
- * lambda_t on the device; k = 0 removes the correction.  Needs a hierarchy of
- * two levels or more with FP64 values.  Synchronises the stream.
+ * by the eigenpair search of amgsym_lrc_setup in the Euclidean inner product
+ * (same steps, tol, seed and ranges), all blocks at once.  For a singular
+ * problem (amgsym_is_singular) the null vector G_inn^{-T} 1 of block 0 is
+ * left out.  Stores Z = G_inn^T V_k and Theta Z with Theta_t = (1 -
+ * lambda_t) / lambda_t on the device; k = 0 removes the correction.  Needs a
+ * hierarchy of two levels or more with FP64 values.  Synchronises the
+ * stream.
  * amgsym_lrcfsai_values: Ritz values (host [2^s][k]) and k, as
  * amgsym_lrc_values.
  *
@@ -344,7 +359,8 @@ amgsym_status amgsym_solve_gmres(amgsym_t h, const double* b_dev, double* x_dev,
  * eq. "LRCFSAI" (use_lrc = 1), FP64, one CG per column (the preconditioner is
  * block diagonal), recurrence residual confirmed by the true residual.
  * ---------------------------------------------------------------------- */
-amgsym_status amgsym_lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, void* stream);
+amgsym_status amgsym_lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, double tol, uint64_t seed,
+                                   void* stream);
 int32_t amgsym_lrcfsai_values(amgsym_t h, double* theta);
 amgsym_status amgsym_solve_fsai(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
                                 const amgsym_solve_opts* sopts, int32_t use_lrc, void* stream,

@@ -151,9 +151,9 @@ def _load():
         "amgsym_fv_assemble": (i32, [i32, pi64, pdbl, pdbl, pi64, pi32, pdbl]),
         "amgsym_fv_assemble_bc": (i32, [i32, pi64, pdbl, pdbl, i32, pi64, pi32, pdbl]),
         "amgsym_is_singular": (i32, [P]),
-        "amgsym_lrc_setup": (i32, [P, i32, i32, ctypes.c_uint64, P]),
+        "amgsym_lrc_setup": (i32, [P, i32, i32, ctypes.c_double, ctypes.c_uint64, P]),
         "amgsym_amgr_apply": (i32, [P, P, P, i32, i32, P]),
-        "amgsym_lrcfsai_setup": (i32, [P, i32, i32, ctypes.c_uint64, P]),
+        "amgsym_lrcfsai_setup": (i32, [P, i32, i32, ctypes.c_double, ctypes.c_uint64, P]),
         "amgsym_lrcfsai_values": (i32, [P, pdbl]),
         "amgsym_solve_fsai": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), i32, P, ctypes.POINTER(SolveInfo)]),
         "amgsym_amgr_info": (i32, [P, pi64, pi64, pi64, pi32, ctypes.POINTER(ctypes.c_int8)]),
@@ -464,9 +464,15 @@ class Problem:
                                      self._stream()))
         return Z
 
-    def lrc_setup(self, k: int, steps: int = 60, seed: int = 7):
-        """LRCAMG(k): the k smallest eigenpairs of M_inn^{-1} A^_i per block (amgsym_lrc_setup)."""
-        _check(lib.amgsym_lrc_setup(self._h, int(k), int(steps), int(seed), self._stream()))
+    @staticmethod
+    def _ritz_steps(k: int, steps: Optional[int]) -> int:
+        return int(steps) if steps is not None else max(40, 2 * int(k) + 8)
+
+    def lrc_setup(self, k: int, steps: Optional[int] = None, tol: float = 0.1, seed: int = 7):
+        """LRCAMG(k): the k smallest eigenpairs of M_inn^{-1} A^_i per block (amgsym_lrc_setup);
+        steps = the restarted Lanczos basis size (default max(40, 2k + 8))."""
+        _check(lib.amgsym_lrc_setup(self._h, int(k), self._ritz_steps(k, steps), float(tol), int(seed),
+                                    self._stream()))
         return self
 
     def lrc_values(self) -> np.ndarray:
@@ -478,9 +484,10 @@ class Problem:
         lib.amgsym_lrc_values(self._h, _ptr(out, ctypes.c_double))
         return out.reshape(self.nb, k)
 
-    def lrcfsai_setup(self, k: int, steps: int = 60, seed: int = 7):
-        """LRCFSAI(k): the k smallest eigenpairs of G_inn A^_i G_inn^T per block."""
-        _check(lib.amgsym_lrcfsai_setup(self._h, int(k), int(steps), int(seed), self._stream()))
+    def lrcfsai_setup(self, k: int, steps: Optional[int] = None, tol: float = 0.1, seed: int = 7):
+        """LRCFSAI(k): the k smallest eigenpairs of G_inn A^_i G_inn^T per block (amgsym_lrcfsai_setup)."""
+        _check(lib.amgsym_lrcfsai_setup(self._h, int(k), self._ritz_steps(k, steps), float(tol), int(seed),
+                                        self._stream()))
         return self
 
     def lrcfsai_values(self) -> np.ndarray:

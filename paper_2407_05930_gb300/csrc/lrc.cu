@@ -13,11 +13,12 @@
 // Theta_t = (1 - lambda_t) / lambda_t.
 //
 // Computing the pairs.  X is self-adjoint in the A^_i inner product, so
-// Lanczos in that inner product (full reorthogonalisation, both Gram-Schmidt
-// passes) gives A^_i-orthonormal Ritz vectors u; then v = A^_i u is the left
-// eigenvector that pairs with u (v^T X = lambda v^T, v^T u = 1).  Every block
-// runs its own Lanczos as one column of the interleaved multi-column layout,
-// so each step is one reduced SpMM and one V-cycle for all blocks at once.
+// Lanczos in that inner product (thick-restarted, with deflated restarts that
+// find every copy of a multiple eigenvalue: ritz_smallest) gives
+// A^_i-orthonormal Ritz vectors u; then v = A^_i u is the left eigenvector
+// that pairs with u (v^T X = lambda v^T, v^T u = 1).  Every block runs its own
+// Lanczos as one column of the interleaved multi-column layout, so each step
+// is one reduced SpMM and one V-cycle for all blocks at once.
 //
 // Application, per column of block i: z = w + U_i (Theta_i V_i^T w) with
 // w = M_inn^{-1} r: k dots and k updates (k_krylov.cu).  The correction is not
@@ -28,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <random>
 #include <string>
 #include <vector>
@@ -116,112 +118,312 @@ void apply_lrc(Device* D, int32_t C, double* z, double* part, double* Hd, cudaSt
   check_launch();
 }
 
+// ---------------------------------------------------------------------------
+// The k smallest eigenpairs of an operator X that is self-adjoint in the
+// inner product <u, v> = u^T B v (B = A^_i for LRCAMG, B = I for LRCFSAI), for every column of the interleaved layout at
+// once (column c is the problem of block c % nb).
+//
+// Lanczos with full reorthogonalisation (two classical Gram-Schmidt passes)
+// keeps the whole projected matrix T = Q^T B X Q from the Gram-Schmidt
+// coefficients, so the basis can be thick-restarted (Wu and Simon's
+// thick-restart Lanczos, SIAM J. Matrix Anal. Appl. 22, 2000) from the `keep`
+// Ritz vectors of the smallest Ritz values and the last Lanczos vector
+// whenever it reaches W vectors, without any special form of T.  A run ends
+// when the k smallest Ritz pairs have residuals ||X u - theta u||_B <=
+// tol * theta (|beta_W y_W| per pair).  One Krylov sequence holds a single
+// copy of a multiple eigenvalue (the mirror blocks of a cube have 3-fold
+// ones, and a correction that misses the copies barely helps), so the search
+// restarts from new random vectors kept B-orthogonal to every pair found so
+// far (deflation by locking) and stops when a run finds nothing below the
+// k-th smallest value found before.  The pairs kept are the k smallest of all
+// runs.  Ritz values at rounding level relative to the largest (a null
+// space) are never kept.
+constexpr int kRitzMaxRuns = 4;
+constexpr int kRitzMaxCycles = 200;
+
+struct RitzOp {
+  bool b_inner = false;                                                       // B-inner product, else Euclidean
+  std::function<void(const double* q, const double* bq, double* out)> apply;  // out = X q (bq = B q)
+  std::function<void(const double* q, double* out)> bmul;                     // out = B q
+};
+
+// Eigenpairs of the leading m x m part of a column's projected matrix,
+// ascending, without the rounding-level ones.
+struct ColRitz {
+  int m = 0;
+  std::vector<double> th, Y;  // th[e], Y[i * m + e]
+  std::vector<int> order;     // all values ascending
+  std::vector<int> usable;    // ascending, rounding-level ones left out
+};
+
+ColRitz col_ritz(const std::vector<double>& T, int W, int col, int m) {
+  ColRitz r;
+  r.m = m;
+  if (m == 0) return r;
+  std::vector<double> A((size_t)m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = T[((size_t)col * W + i) * W + j];
+  jacobi_eig(A, r.Y, m);
+  r.th.resize(m);
+  for (int e = 0; e < m; ++e) r.th[e] = A[(size_t)e * m + e];
+  r.order.resize(m);
+  for (int e = 0; e < m; ++e) r.order[e] = e;
+  std::sort(r.order.begin(), r.order.end(), [&](int a, int b) { return r.th[a] < r.th[b]; });
+  double top = 0.0;
+  for (double v : r.th) top = std::max(top, std::fabs(v));
+  for (int e : r.order)
+    if (r.th[e] > 1e-10 * top) r.usable.push_back(e);
+  return r;
+}
+
+// U (and BU = B U when op.b_inner): k vectors of n_b x C; vector t holds in
+// column c the t-th smallest pair of column c (zero where the column has
+// fewer), theta[c * k + t] its Ritz value (0 where none).  lock0: n0
+// B-orthonormal vectors (B lock0 = lock0b) every pair stays B-orthogonal to.
+void ritz_smallest(const Ctx& c, const RitzOp& op, int k, int W, double tol, uint64_t seed, const double* lock0,
+                   const double* lock0b, int n0, double* U, double* BU, std::vector<double>& theta) {
+  Device* D = c.D;
+  cudaStream_t st = c.st;
+  const int32_t C = c.C;
+  const int64_t n_b = D->n_b, len = n_b * C;
+  const bool bi = op.b_inner;
+  const int keep = std::min(W - 2, std::max(k + 4, W / 2));
+  const int pcap = kRitzMaxRuns * k;
+  const int jmax = std::max(std::max(W + 1, pcap), std::max(n0, 1));
+  DevBuf QA((int64_t)(W + 1) * len), QB((int64_t)(W + 1) * len), BQA(bi ? (int64_t)(W + 1) * len : 0),
+      BQB(bi ? (int64_t)(W + 1) * len : 0), pool((int64_t)pcap * len), bpool(bi ? (int64_t)pcap * len : 0), w(len),
+      bw(bi ? len : 0), part((int64_t)mdot_blocks(n_b, C) * jmax * C), Hd((int64_t)2 * (W + 1) * C),
+      Hl((int64_t)jmax * C), Hc((int64_t)std::max(keep, k) * jmax * C), sd(C);
+  double* qa = QA.p;
+  double* qb = QB.p;
+  double* bqa = bi ? BQA.p : QA.p;
+  double* bqb = bi ? BQB.p : QB.p;
+  double* bp = bi ? bpool.p : pool.p;
+  double* bwp = bi ? bw.p : w.p;
+  std::vector<double> hh((size_t)2 * (W + 1) * C), sv(C), b2(C);
+  std::vector<double> pool_theta((size_t)pcap * C, HUGE_VAL);
+  int P = 0;
+
+  // w -= V (BV^T w) for a B-orthonormal set of J vectors
+  auto orth_set = [&](const double* V, const double* BV, int J) {
+    if (J <= 0) return;
+    launch_mdot(BV, len, C, J, w.p, n_b, C, part.p, Hl.p, st);
+    launch_maxpy(V, len, C, J, Hl.p, -1.0, w.p, n_b, C, st);
+  };
+  auto norm2 = [&]() {  // b2 = w^T B w per column (bw = B w)
+    if (bi) op.bmul(w.p, bw.p);
+    launch_mdot(w.p, 0, C, 1, bwp, n_b, C, part.p, Hl.p, st);
+    check_launch();
+    to_host(b2.data(), Hl.p, C, st);
+  };
+  auto put_scaled = [&](double* q, double* bq) {  // q = w * sv, bq = B w * sv
+    to_dev(sd.p, sv.data(), C, st);
+    launch_colscale(w.p, sd.p, q, n_b, C, st);
+    if (bi) launch_colscale(bw.p, sd.p, bq, n_b, C, st);
+    check_launch();
+  };
+  // dst_t = sum_j src_j coef[t][j][c], t < nt (coef [nt][J][C], uploaded)
+  auto combine = [&](const double* src, int J, const std::vector<double>& coef, int nt, double* dst) {
+    to_dev(Hc.p, coef.data(), (int64_t)nt * J * C, st);
+    for (int t = 0; t < nt; ++t) {
+      CK(cudaMemsetAsync(dst + (int64_t)t * len, 0, sizeof(double) * (size_t)len, st));
+      launch_maxpy(src, len, C, J, Hc.p + (int64_t)t * J * C, 1.0, dst + (int64_t)t * len, n_b, C, st);
+    }
+    check_launch();
+  };
+
+  for (int run = 0; run < kRitzMaxRuns; ++run) {
+    // start vector: uniform[-1, 1], B-orthogonal to the locked vectors
+    {
+      std::vector<double> q0((size_t)len);
+      std::mt19937_64 rng(seed + 0x9E3779B97F4A7C15ull * (uint64_t)run);
+      std::uniform_real_distribution<double> Ud(-1.0, 1.0);
+      for (auto& v : q0) v = Ud(rng);
+      to_dev(w.p, q0.data(), len, st);
+    }
+    norm2();
+    const std::vector<double> b2_start = b2;
+    for (int pass = 0; pass < 2; ++pass) {
+      orth_set(lock0, lock0b, n0);
+      orth_set(pool.p, bp, P);
+    }
+    check_launch();
+    norm2();
+    std::vector<char> open(C, 0);
+    bool any_open = false;
+    for (int col = 0; col < C; ++col) {
+      open[col] = b2[col] > 1e-20 * b2_start[col];  // else the locked vectors span the column's space
+      sv[col] = open[col] ? 1.0 / std::sqrt(b2[col]) : 0.0;
+      any_open = any_open || open[col];
+    }
+    if (!any_open) break;
+    put_scaled(qa, bqa);
+    std::vector<double> T((size_t)C * W * W, 0.0), beta(C, 0.0), tscale(C, 0.0);
+    std::vector<int> valid(C, 0);
+    std::vector<ColRitz> rz(C);
+    int nk = 0;
+    for (int cycle = 0;; ++cycle) {
+      for (int j = nk; j < W; ++j) {
+        op.apply(qa + (int64_t)j * len, bqa + (int64_t)j * len, w.p);
+        for (int pass = 0; pass < 2; ++pass) {
+          orth_set(lock0, lock0b, n0);
+          orth_set(pool.p, bp, P);
+          double* hp = Hd.p + (int64_t)pass * (W + 1) * C;
+          launch_mdot(bqa, len, C, j + 1, w.p, n_b, C, part.p, hp, st);
+          launch_maxpy(qa, len, C, j + 1, hp, -1.0, w.p, n_b, C, st);
+        }
+        check_launch();
+        to_host(hh.data(), Hd.p, (int64_t)2 * (W + 1) * C, st);
+        norm2();
+        for (int col = 0; col < C; ++col) {
+          sv[col] = 0.0;
+          if (!open[col]) continue;
+          for (int i = 0; i <= j; ++i) {
+            const double t = hh[(size_t)i * C + col] + hh[(size_t)(W + 1 + i) * C + col];
+            T[((size_t)col * W + i) * W + j] = T[((size_t)col * W + j) * W + i] = t;
+            tscale[col] = std::max(tscale[col], std::fabs(t));
+          }
+          valid[col] = j + 1;
+          const double b = std::sqrt(std::max(b2[col], 0.0));
+          if (b > 1e-10 * tscale[col]) {
+            beta[col] = b;
+            sv[col] = 1.0 / b;
+          } else {  // invariant subspace: the column's Ritz pairs are exact
+            beta[col] = 0.0;
+            open[col] = 0;
+          }
+        }
+        put_scaled(qa + (int64_t)(j + 1) * len, bqa + (int64_t)(j + 1) * len);
+      }
+      bool conv = true;
+      for (int col = 0; col < C; ++col) {
+        rz[col] = col_ritz(T, W, col, valid[col]);
+        const ColRitz& r = rz[col];
+        const int nk_c = std::min<int>(k, (int)r.usable.size());
+        for (int t = 0; t < nk_c && open[col]; ++t) {
+          const int e = r.usable[t];
+          if (!(std::fabs(beta[col] * r.Y[(size_t)(r.m - 1) * r.m + e]) <= tol * std::fabs(r.th[e]))) conv = false;
+        }
+      }
+      if (conv || cycle + 1 >= kRitzMaxCycles) break;
+      // thick restart: the keep smallest Ritz vectors, then the last Lanczos vector
+      std::vector<double> coef((size_t)keep * W * C, 0.0);
+      for (int col = 0; col < C; ++col) {
+        const ColRitz& r = rz[col];
+        for (int t = 0; t < keep && t < r.m; ++t)
+          for (int i = 0; i < r.m; ++i) coef[((size_t)t * W + i) * C + col] = r.Y[(size_t)i * r.m + r.order[t]];
+      }
+      combine(qa, W, coef, keep, qb);
+      if (bi) combine(bqa, W, coef, keep, bqb);
+      CK(cudaMemcpyAsync(qb + (int64_t)keep * len, qa + (int64_t)W * len, sizeof(double) * (size_t)len,
+                         cudaMemcpyDeviceToDevice, st));
+      if (bi)
+        CK(cudaMemcpyAsync(bqb + (int64_t)keep * len, bqa + (int64_t)W * len, sizeof(double) * (size_t)len,
+                           cudaMemcpyDeviceToDevice, st));
+      std::swap(qa, qb);
+      std::swap(bqa, bqb);
+      std::fill(T.begin(), T.end(), 0.0);
+      for (int col = 0; col < C; ++col) {
+        const ColRitz& r = rz[col];
+        valid[col] = std::min(keep, r.m);
+        tscale[col] = 0.0;
+        for (int t = 0; t < valid[col]; ++t) {
+          const double th = r.th[r.order[t]];
+          T[((size_t)col * W + t) * W + t] = th;
+          tscale[col] = std::max(tscale[col], std::fabs(th));
+        }
+      }
+      nk = keep;
+    }
+    // the run's k smallest pairs join the locked pool
+    std::vector<double> coef((size_t)k * W * C, 0.0);
+    bool any_new = false;
+    for (int col = 0; col < C; ++col) {
+      const ColRitz& r = rz[col];
+      std::vector<double> prev;
+      for (int p = 0; p < P; ++p)
+        if (pool_theta[(size_t)p * C + col] < HUGE_VAL) prev.push_back(pool_theta[(size_t)p * C + col]);
+      std::sort(prev.begin(), prev.end());
+      const double kth = (int)prev.size() >= k ? prev[k - 1] : HUGE_VAL;
+      for (int t = 0; t < k && t < (int)r.usable.size(); ++t) {
+        const int e = r.usable[t];
+        for (int i = 0; i < r.m; ++i) coef[((size_t)t * W + i) * C + col] = r.Y[(size_t)i * r.m + e];
+        pool_theta[(size_t)(P + t) * C + col] = r.th[e];
+        if (r.th[e] < kth) any_new = true;
+      }
+    }
+    combine(qa, W, coef, k, pool.p + (int64_t)P * len);
+    if (bi) combine(bqa, W, coef, k, bpool.p + (int64_t)P * len);
+    P += k;
+    if (!any_new) break;
+  }
+  // the k smallest of every run, gathered per column
+  theta.assign((size_t)C * k, 0.0);
+  std::vector<double> sel((size_t)k * std::max(P, 1) * C, 0.0);
+  for (int col = 0; col < C; ++col) {
+    std::vector<int> idx;
+    for (int p = 0; p < P; ++p)
+      if (pool_theta[(size_t)p * C + col] < HUGE_VAL) idx.push_back(p);
+    std::sort(idx.begin(), idx.end(),
+              [&](int a, int b) { return pool_theta[(size_t)a * C + col] < pool_theta[(size_t)b * C + col]; });
+    for (int t = 0; t < k && t < (int)idx.size(); ++t) {
+      sel[((size_t)t * P + idx[t]) * C + col] = 1.0;
+      theta[(size_t)col * k + t] = pool_theta[(size_t)idx[t] * C + col];
+    }
+  }
+  if (P > 0) {
+    combine(pool.p, P, sel, k, U);
+    if (bi) combine(bpool.p, P, sel, k, BU);
+  } else {
+    CK(cudaMemsetAsync(U, 0, sizeof(double) * (size_t)k * len, st));
+    if (bi) CK(cudaMemsetAsync(BU, 0, sizeof(double) * (size_t)k * len, st));
+  }
+  CK(cudaStreamSynchronize(st));
+}
+
 }  // namespace
 
-// Lanczos in the A^_i inner product on X = M_inn^{-1} A^_i for all blocks at
-// once; keeps the k Ritz pairs of the smallest Ritz values.
-static void lrc_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, cudaStream_t st) {
+// LRCAMG(k) setup: X = M_inn^{-1} A^_i is self-adjoint in the A^_i inner
+// product; its k smallest eigenpairs per block give U (A^_i-orthonormal) and
+// V_t = Theta_t A^_i u_t.
+static void lrc_setup(amgsym_t h, int32_t k, int32_t steps, double tol, uint64_t seed, cudaStream_t st) {
   Device* D = require_dev(h);
   D->lrc_k = 0;
   D->lrc_U = D->lrc_V = nullptr;  // the old arrays stay owned until device_free
   D->lrc_theta.clear();
   if (k == 0) return;
-  const int32_t nb = D->nb, C = nb;
+  const int32_t C = D->nb;
   const int64_t n_b = D->n_b, len = n_b * C;
-  const int m = steps;
   ensure_work(D, 1, VEC_F64);
   Ctx c{D, C, VEC_F64, VAL_F64, false, st};
   c.fuse = true;
-  DevBuf Q((int64_t)(m + 1) * len), AQ((int64_t)(m + 1) * len), w(len), part((int64_t)mdot_blocks(n_b, C) * (m + 1) * C),
-      Hd((int64_t)(m + 1) * C), sd(C);
-  // start vector: uniform[-1, 1] from the seed
-  {
-    std::vector<double> q0((size_t)len);
-    std::mt19937_64 rng(seed);
-    std::uniform_real_distribution<double> U(-1.0, 1.0);
-    for (auto& v : q0) v = U(rng);
-    to_dev(Q.p, q0.data(), len, st);
-  }
-  std::vector<double> hh((size_t)(m + 1) * C), sv(C);
-  auto normalise = [&](double* q, double* aq) {  // q, aq *= 1 / sqrt(q^T A^ q), per column
-    launch_mdot(q, 0, C, 1, aq, n_b, C, part.p, Hd.p, st);
-    check_launch();
-    to_host(hh.data(), Hd.p, C, st);
-    for (int j = 0; j < C; ++j) sv[j] = hh[j] > 0.0 ? 1.0 / std::sqrt(hh[j]) : 0.0;
-    to_dev(sd.p, sv.data(), C, st);
-    launch_colscale(q, sd.p, q, n_b, C, st);
-    launch_colscale(aq, sd.p, aq, n_b, C, st);
-    check_launch();
-    return hh;
+  RitzOp op;
+  op.b_inner = true;
+  op.bmul = [&](const double* q, double* out) {
+    spmm(c, D->Ainn, VAL_F64, VEC_F64, VEC_F64, q, out, 1.0, 0.0, nullptr, true, nullptr);
   };
-  spmm(c, D->Ainn, VAL_F64, VEC_F64, VEC_F64, Q.p, AQ.p, 1.0, 0.0, nullptr, true, nullptr);
-  normalise(Q.p, AQ.p);
-  std::vector<double> alpha((size_t)m * C, 0.0), beta((size_t)m * C, 0.0);
-  std::vector<int> mc(C, m);  // Lanczos steps taken per column (an invariant subspace ends it early)
-  for (int j = 0; j < m; ++j) {
-    double* aqj = AQ.p + (int64_t)j * len;
-    vcycle_apply(c, aqj, w.p);  // w = M_inn^{-1} A^ q_j
+  op.apply = [&](const double*, const double* bq, double* out) {  // M_inn^{-1} (A^ q)
+    vcycle_apply(c, bq, out);
     check_launch();
-    std::vector<double> h_sum((size_t)(j + 1) * C, 0.0);
-    for (int pass = 0; pass < 2; ++pass) {  // w -= Q (AQ^T w), twice
-      launch_mdot(AQ.p, len, C, j + 1, w.p, n_b, C, part.p, Hd.p, st);
-      launch_maxpy(Q.p, len, C, j + 1, Hd.p, -1.0, w.p, n_b, C, st);
-      check_launch();
-      to_host(hh.data(), Hd.p, (int64_t)(j + 1) * C, st);
-      for (int64_t t = 0; t < (int64_t)(j + 1) * C; ++t) h_sum[t] += hh[t];
-    }
-    for (int col = 0; col < C; ++col) alpha[(size_t)j * C + col] = h_sum[(size_t)j * C + col];
-    double* qn = Q.p + (int64_t)(j + 1) * len;
-    double* aqn = AQ.p + (int64_t)(j + 1) * len;
-    CK(cudaMemcpyAsync(qn, w.p, sizeof(double) * (size_t)len, cudaMemcpyDeviceToDevice, st));
-    spmm(c, D->Ainn, VAL_F64, VEC_F64, VEC_F64, qn, aqn, 1.0, 0.0, nullptr, true, nullptr);
-    const std::vector<double> b2 = normalise(qn, aqn);
-    for (int col = 0; col < C; ++col) {
-      double amax = 0.0;
-      for (int i = 0; i <= j; ++i) amax = std::max(amax, std::fabs(alpha[(size_t)i * C + col]));
-      const double b = b2[col] > 0.0 ? std::sqrt(b2[col]) : 0.0;
-      beta[(size_t)j * C + col] = b;
-      if (mc[col] == m && !(b > 1e-10 * amax)) mc[col] = j + 1;  // invariant subspace: T is complete
-    }
-  }
-  // Ritz pairs per column; the k smallest (or all the column has)
-  std::vector<double> theta((size_t)C * k, 0.0), Y((size_t)m * k * C, 0.0), Yv((size_t)m * k * C, 0.0);
-  for (int col = 0; col < C; ++col) {
-    const int mm = mc[col];
-    std::vector<double> T((size_t)mm * mm, 0.0), V;
-    for (int i = 0; i < mm; ++i) {
-      T[(size_t)i * mm + i] = alpha[(size_t)i * C + col];
-      if (i + 1 < mm) T[(size_t)i * mm + i + 1] = T[(size_t)(i + 1) * mm + i] = beta[(size_t)i * C + col];
-    }
-    jacobi_eig(T, V, mm);
-    std::vector<int> order(mm);
-    for (int i = 0; i < mm; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return T[(size_t)a * mm + a] < T[(size_t)b * mm + b]; });
-    for (int t = 0; t < k && t < mm; ++t) {
-      const int e = order[t];
-      const double th = T[(size_t)e * mm + e];
-      theta[(size_t)col * k + t] = th;
-      const double Th = th > 0.0 ? (1.0 - th) / th : 0.0;  // Theta_t of eq. "LRC_AMG"
-      for (int i = 0; i < mm; ++i) {
-        Y[((size_t)t * m + i) * C + col] = V[(size_t)i * mm + e];
-        Yv[((size_t)t * m + i) * C + col] = Th * V[(size_t)i * mm + e];
-      }
-    }
-  }
-  // U_t = Q Y_t and V_t = Theta_t A^ U_t = (A^ Q) Theta_t Y_t, stored [k][n_b][nb]
+  };
   double* U = nullptr;
   double* Vv = nullptr;
   CK(cudaMalloc(&U, sizeof(double) * (size_t)k * len));
   D->owned.push_back(U);
   CK(cudaMalloc(&Vv, sizeof(double) * (size_t)k * len));
   D->owned.push_back(Vv);
-  CK(cudaMemsetAsync(U, 0, sizeof(double) * (size_t)k * len, st));
-  CK(cudaMemsetAsync(Vv, 0, sizeof(double) * (size_t)k * len, st));
+  std::vector<double> theta;
+  ritz_smallest(c, op, k, steps, tol, seed, nullptr, nullptr, 0, U, Vv, theta);
+  // V_t = Theta_t A^ u_t with Theta_t = (1 - lambda_t) / lambda_t (eq. "LRC_AMG")
+  DevBuf sd(C);
+  std::vector<double> th(C);
   for (int t = 0; t < k; ++t) {
-    to_dev(Hd.p, Y.data() + (size_t)t * m * C, (int64_t)m * C, st);
-    launch_maxpy(Q.p, len, C, m, Hd.p, 1.0, U + (int64_t)t * len, n_b, C, st);
-    to_dev(Hd.p, Yv.data() + (size_t)t * m * C, (int64_t)m * C, st);
-    launch_maxpy(AQ.p, len, C, m, Hd.p, 1.0, Vv + (int64_t)t * len, n_b, C, st);
+    for (int col = 0; col < C; ++col) {
+      const double l = theta[(size_t)col * k + t];
+      th[col] = l > 0.0 ? (1.0 - l) / l : 0.0;
+    }
+    to_dev(sd.p, th.data(), C, st);
+    launch_colscale(Vv + (int64_t)t * len, sd.p, Vv + (int64_t)t * len, n_b, C, st);
     check_launch();
   }
   CK(cudaStreamSynchronize(st));
@@ -387,11 +589,11 @@ static amgsym_status gmres_impl(amgsym_t h, const double* b_dev, double* x_dev, 
 // eigenvalues (V_k, Lambda_k), Y = I - X has Sigma = I - Lambda and the
 // correction is Z_k Theta_k Z_k^T with Z_k = G_inn^T V_k and
 // Theta = Sigma (I - Sigma)^{-1}: Theta_t = (1 - lambda_t) / lambda_t.  The
-// pairs come from Lanczos on X (Euclidean inner product, full
-// reorthogonalisation) for all blocks at once; the preconditioner is
-// symmetric, so the solve is PCG.
+// pairs come from the restarted Lanczos of ritz_smallest on X (Euclidean inner
+// product) for all blocks at once; the preconditioner is symmetric, so the
+// solve is PCG.
 
-static void lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, cudaStream_t st) {
+static void lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, double tol, uint64_t seed, cudaStream_t st) {
   Device* D = require_dev(h);
   D->lrcf_k = 0;
   D->lrcf_Z = D->lrcf_TZ = nullptr;
@@ -401,96 +603,59 @@ static void lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, c
   if (L.cinv || !L.G.v64 || !L.Gt.v64)
     fail(AMGSYM_ERR_STATE, "LRCFSAI needs the FP64 FSAI factor of A_inn (a hierarchy of two levels or more, "
                            "opts.precisions with FP64)");
-  const int32_t nb = D->nb, C = nb;
+  const int32_t C = D->nb;
   const int64_t n_b = D->n_b, len = n_b * C;
-  const int m = steps;
   ensure_work(D, 1, VEC_F64);
   Ctx c{D, C, VEC_F64, VAL_F64, false, st};
   PrecWork& W = D->w64;
-  DevBuf Q((int64_t)(m + 1) * len), w(len), part((int64_t)mdot_blocks(n_b, C) * (m + 1) * C), Hd((int64_t)(m + 1) * C),
-      sd(C);
-  {
-    std::vector<double> q0((size_t)len);
-    std::mt19937_64 rng(seed);
-    std::uniform_real_distribution<double> U(-1.0, 1.0);
-    for (auto& v : q0) v = U(rng);
-    to_dev(Q.p, q0.data(), len, st);
-  }
-  std::vector<double> hh((size_t)(m + 1) * C), sv(C);
-  auto normalise = [&](double* q) {  // q /= ||q|| per column; returns ||q||^2
-    launch_mdot(q, 0, C, 1, q, n_b, C, part.p, Hd.p, st);
-    check_launch();
-    to_host(hh.data(), Hd.p, C, st);
-    for (int j = 0; j < C; ++j) sv[j] = hh[j] > 0.0 ? 1.0 / std::sqrt(hh[j]) : 0.0;
-    to_dev(sd.p, sv.data(), C, st);
-    launch_colscale(q, sd.p, q, n_b, C, st);
-    check_launch();
-    return std::vector<double>(hh.begin(), hh.begin() + C);
-  };
-  auto apply_X = [&](const double* q, double* out) {  // out = G A^ G^T q
+  RitzOp op;
+  op.apply = [&](const double* q, const double*, double* out) {  // G A^ G^T q
     spmm(c, L.Gt, VAL_F64, VEC_F64, VEC_F64, q, W.z, 1.0, 0.0, nullptr, false, nullptr);
     spmm(c, D->Ainn, VAL_F64, VEC_F64, VEC_F64, W.z, W.q, 1.0, 0.0, nullptr, true, nullptr);
     spmm(c, L.G, VAL_F64, VEC_F64, VEC_F64, W.q, out, 1.0, 0.0, nullptr, false, nullptr);
   };
-  normalise(Q.p);
-  std::vector<double> alpha((size_t)m * C, 0.0), beta((size_t)m * C, 0.0);
-  std::vector<int> mc(C, m);
-  for (int j = 0; j < m; ++j) {
-    apply_X(Q.p + (int64_t)j * len, w.p);
-    std::vector<double> h_sum((size_t)(j + 1) * C, 0.0);
-    for (int pass = 0; pass < 2; ++pass) {
-      launch_mdot(Q.p, len, C, j + 1, w.p, n_b, C, part.p, Hd.p, st);
-      launch_maxpy(Q.p, len, C, j + 1, Hd.p, -1.0, w.p, n_b, C, st);
-      check_launch();
-      to_host(hh.data(), Hd.p, (int64_t)(j + 1) * C, st);
-      for (int64_t t = 0; t < (int64_t)(j + 1) * C; ++t) h_sum[t] += hh[t];
+  // A singular block 0 (A^_0 1 = 0) gives X the null vector G^{-T} 1, found
+  // by back substitution with the lower-triangular host factor; the pairs stay
+  // orthogonal to it.
+  DevBuf nullv(D->singular ? len : 0);
+  if (D->singular) {
+    const Csr& G = h->H.levels[0].G;
+    std::vector<double> r((size_t)n_b, 1.0), v((size_t)n_b, 0.0);
+    for (int64_t i = n_b - 1; i >= 0; --i) {
+      double d = 0.0;
+      for (int64_t e = G.ptr[i]; e < G.ptr[i + 1]; ++e)
+        if (G.idx[e] == i) d = G.val[e];
+      if (!(d != 0.0)) fail(AMGSYM_ERR_STATE, "FSAI factor with a zero diagonal");
+      v[i] = r[i] / d;
+      for (int64_t e = G.ptr[i]; e < G.ptr[i + 1]; ++e)
+        if (G.idx[e] < i) r[G.idx[e]] -= G.val[e] * v[i];
     }
-    for (int col = 0; col < C; ++col) alpha[(size_t)j * C + col] = h_sum[(size_t)j * C + col];
-    double* qn = Q.p + (int64_t)(j + 1) * len;
-    CK(cudaMemcpyAsync(qn, w.p, sizeof(double) * (size_t)len, cudaMemcpyDeviceToDevice, st));
-    const std::vector<double> b2 = normalise(qn);
-    for (int col = 0; col < C; ++col) {
-      double amax = 0.0;
-      for (int i = 0; i <= j; ++i) amax = std::max(amax, std::fabs(alpha[(size_t)i * C + col]));
-      const double b = b2[col] > 0.0 ? std::sqrt(b2[col]) : 0.0;
-      beta[(size_t)j * C + col] = b;
-      if (mc[col] == m && !(b > 1e-10 * amax)) mc[col] = j + 1;
-    }
+    double nv = 0.0;
+    for (double x : v) nv += x * x;
+    nv = std::sqrt(nv);
+    std::vector<double> hv((size_t)len, 0.0);
+    for (int64_t i = 0; i < n_b; ++i) hv[(size_t)i * C] = v[i] / nv;  // column 0: block 0
+    to_dev(nullv.p, hv.data(), len, st);
   }
-  std::vector<double> theta((size_t)C * k, 0.0), Y((size_t)m * k * C, 0.0);
-  std::vector<double> Th((size_t)k * C, 0.0);
-  for (int col = 0; col < C; ++col) {
-    const int mm = mc[col];
-    std::vector<double> T((size_t)mm * mm, 0.0), V;
-    for (int i = 0; i < mm; ++i) {
-      T[(size_t)i * mm + i] = alpha[(size_t)i * C + col];
-      if (i + 1 < mm) T[(size_t)i * mm + i + 1] = T[(size_t)(i + 1) * mm + i] = beta[(size_t)i * C + col];
-    }
-    jacobi_eig(T, V, mm);
-    std::vector<int> order(mm);
-    for (int i = 0; i < mm; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return T[(size_t)a * mm + a] < T[(size_t)b * mm + b]; });
-    for (int t = 0; t < k && t < mm; ++t) {
-      const int e = order[t];
-      const double th = T[(size_t)e * mm + e];
-      theta[(size_t)col * k + t] = th;
-      Th[(size_t)t * C + col] = th > 0.0 ? (1.0 - th) / th : 0.0;  // Sigma (I - Sigma)^{-1}
-      for (int i = 0; i < mm; ++i) Y[((size_t)t * m + i) * C + col] = V[(size_t)i * mm + e];
-    }
-  }
-  // Z_t = G^T (Q Y_t), Theta Z_t
+  DevBuf Uu((int64_t)k * len), sd(C);
+  std::vector<double> theta;
+  ritz_smallest(c, op, k, steps, tol, seed, nullv.p, nullv.p, D->singular ? 1 : 0, Uu.p, nullptr, theta);
+  // Z_t = G^T u_t and Theta_t Z_t, Theta_t = (1 - lambda_t) / lambda_t
   double* Z = nullptr;
   double* TZ = nullptr;
   CK(cudaMalloc(&Z, sizeof(double) * (size_t)k * len));
   D->owned.push_back(Z);
   CK(cudaMalloc(&TZ, sizeof(double) * (size_t)k * len));
   D->owned.push_back(TZ);
+  std::vector<double> th(C);
   for (int t = 0; t < k; ++t) {
-    CK(cudaMemsetAsync(w.p, 0, sizeof(double) * (size_t)len, st));
-    to_dev(Hd.p, Y.data() + (size_t)t * m * C, (int64_t)m * C, st);
-    launch_maxpy(Q.p, len, C, m, Hd.p, 1.0, w.p, n_b, C, st);
-    spmm(c, L.Gt, VAL_F64, VEC_F64, VEC_F64, w.p, Z + (int64_t)t * len, 1.0, 0.0, nullptr, false, nullptr);
-    to_dev(sd.p, Th.data() + (size_t)t * C, C, st);
+    spmm(c, L.Gt, VAL_F64, VEC_F64, VEC_F64, Uu.p + (int64_t)t * len, Z + (int64_t)t * len, 1.0, 0.0, nullptr, false,
+         nullptr);
+    for (int col = 0; col < C; ++col) {
+      const double l = theta[(size_t)col * k + t];
+      th[col] = l > 0.0 ? (1.0 - l) / l : 0.0;  // Sigma (I - Sigma)^{-1}
+    }
+    to_dev(sd.p, th.data(), C, st);
     launch_colscale(Z + (int64_t)t * len, sd.p, TZ + (int64_t)t * len, n_b, C, st);
     check_launch();
   }
@@ -625,12 +790,14 @@ static amgsym_status fsai_pcg_impl(amgsym_t h, const double* b_dev, double* x_de
 
 using namespace amgsym;
 
-extern "C" amgsym_status amgsym_lrc_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, void* stream) {
+extern "C" amgsym_status amgsym_lrc_setup(amgsym_t h, int32_t k, int32_t steps, double tol, uint64_t seed,
+                                          void* stream) {
   try {
     if (!h) fail(AMGSYM_ERR_ARG, "NULL handle");
     if (k < 0 || k > 64) fail(AMGSYM_ERR_ARG, "k must be in [0, 64]");
-    if (k > 0 && (steps < k || steps > 400)) fail(AMGSYM_ERR_ARG, "steps must be in [k, 400]");
-    lrc_setup(h, k, steps, seed, static_cast<cudaStream_t>(stream));
+    if (k > 0 && (steps < k + 2 || steps > 400)) fail(AMGSYM_ERR_ARG, "steps must be in [k + 2, 400]");
+    if (k > 0 && !(tol > 0.0 && tol <= 1.0)) fail(AMGSYM_ERR_ARG, "tol must be in (0, 1]");
+    lrc_setup(h, k, steps, tol, seed, static_cast<cudaStream_t>(stream));
     return AMGSYM_OK;
   } catch (const amgsym::Error& e) {
     amgsym::set_last_error(e.msg);
@@ -662,12 +829,14 @@ extern "C" amgsym_status amgsym_solve_gmres(amgsym_t h, const double* b_dev, dou
   }
 }
 
-extern "C" amgsym_status amgsym_lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, uint64_t seed, void* stream) {
+extern "C" amgsym_status amgsym_lrcfsai_setup(amgsym_t h, int32_t k, int32_t steps, double tol, uint64_t seed,
+                                              void* stream) {
   try {
     if (!h) fail(AMGSYM_ERR_ARG, "NULL handle");
     if (k < 0 || k > 64) fail(AMGSYM_ERR_ARG, "k must be in [0, 64]");
-    if (k > 0 && (steps < k || steps > 400)) fail(AMGSYM_ERR_ARG, "steps must be in [k, 400]");
-    lrcfsai_setup(h, k, steps, seed, static_cast<cudaStream_t>(stream));
+    if (k > 0 && (steps < k + 2 || steps > 400)) fail(AMGSYM_ERR_ARG, "steps must be in [k + 2, 400]");
+    if (k > 0 && !(tol > 0.0 && tol <= 1.0)) fail(AMGSYM_ERR_ARG, "tol must be in (0, 1]");
+    lrcfsai_setup(h, k, steps, tol, seed, static_cast<cudaStream_t>(stream));
     return AMGSYM_OK;
   } catch (const amgsym::Error& e) {
     amgsym::set_last_error(e.msg);

@@ -37,7 +37,7 @@ def test_ritz_values_with_an_exact_inner_solve(s):
     P = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=4096)
     assert P.num_levels() == 1
     kk = 6
-    P.lrc_setup(kk, steps=80, seed=3)
+    P.lrc_setup(kk, steps=80, tol=1e-10, seed=3)
     theta = P.lrc_values()
     assert theta.shape == (1 << s, kk)
     H = symmetry.blocks(A, symmetry.mirror_perm(N, s))
@@ -46,9 +46,9 @@ def test_ritz_values_with_an_exact_inner_solve(s):
     checked = 0
     for i, Ai in enumerate(hat):
         lam = np.sort(np.linalg.eigvals(Binv @ Ai.toarray()).real)[:kk]
-        # eigenvalue 1 is multiple (every direction away from the mirror
-        # planes); Lanczos finds a multiple eigenvalue once, so compare the
-        # blocks whose kk smallest eigenvalues lie below it and are simple
+        # eigenvalue 1 is highly multiple (every direction away from the
+        # mirror planes) and each search run finds one copy of it, so compare
+        # the blocks whose kk smallest eigenvalues lie below it
         if lam[-1] >= 1.0 - 1e-6:
             assert theta[i][0] >= 1.0 - 1e-8, (i, theta[i])
             continue
@@ -101,7 +101,7 @@ def test_model_problem_iterations_fall_with_k():
         b -= b.mean()
         row = []
         for k in (0, 4, 16):
-            P.lrc_setup(k, steps=max(40, 3 * k))
+            P.lrc_setup(k)
             x, info = P.solve_gmres(torch.from_numpy(b).to(DEV), restart=60, lrc=k > 0, tol=1e-8, maxit=300)
             assert info.converged
             r = b - fv.apply(h, np.ones(P.n), x.cpu().numpy(), "neumann")
