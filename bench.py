@@ -70,7 +70,8 @@ PROFILED_TRAFFIC = {
     "coarse_kernel<float>": 94208,
 }
 KERNEL_SOURCES = ("paper_2407_05930_gb300/csrc/k_spmm.cu", "paper_2407_05930_gb300/csrc/spmm_common.cuh",
-                  "paper_2407_05930_gb300/csrc/k_misc.cu", "paper_2407_05930_gb300/csrc/dot.cuh")
+                  "paper_2407_05930_gb300/csrc/k_misc.cu", "paper_2407_05930_gb300/csrc/dot.cuh",
+                  "paper_2407_05930_gb300/csrc/stencil.cuh", "paper_2407_05930_gb300/csrc/coarse.cuh")
 KERNEL_SOURCES_SHA256 = "8a8f0a7540338d5c8e25bd69ec1230ad3aec8948e8365bf148a6c8dd9dd98674"
 
 

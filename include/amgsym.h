@@ -142,6 +142,22 @@ typedef struct {
                                iterations on the 32^3 model problem against 9-11 for k = 1
                                (the paper pairs k = 2 with DPLS + energy minimisation) */
   int32_t amgr_interp_max;  /* AMGR interpolation weights kept per row, default 4 */
+  int32_t zmarch;           /* 1: a finest-level diagonal-offset product whose
+                               offsets are {0, +-1, +-gx, +-gxy} (a structured grid's 7-point
+                               stencil: the reduced operator A^ and A_inn, or its FSAI factors
+                               G, G^T) runs as a z-marching stencil: a block stages one plane
+                               of X with its halo in shared memory and walks the third grid
+                               index, reading each X row about 1.3 times instead of 7.  Every
+                               neighbour is addressed by its row index like the diagonal-offset
+                               kernel, so the products are bit-identical to it (a fused dot
+                               agrees to rounding: other rows per thread).  Used for FP32
+                               vectors with 8 columns (one RHS at s = 3), gx a multiple of 32
+                               and gxy / gx of 8.  0 (default) = the diagonal-offset kernel
+                               only: at 256^3 the stencil form took 39-41 us for G against
+                               33 us (it holds 512 rows in flight per SM at 110-128 registers
+                               and waits one round trip and a barrier per plane; the
+                               diagonal-offset kernel keeps as many rows in flight without
+                               barriers), 71.1 ms a solve against 67.4 ms */
 } amgsym_opts;
 
 #define AMGSYM_MAX_DIAG 8

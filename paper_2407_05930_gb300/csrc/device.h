@@ -159,6 +159,9 @@ struct SpmmArgs {
   int32_t doff[kMaxDiag] = {}, dsrc[kMaxDiag] = {}, dshift[kMaxDiag] = {};
   int64_t dstride = 0;
   const void* dval = nullptr;
+  // z-marching stencil form of a diagonal-offset matrix (stencil.cuh): its
+  // offsets are {0, +-1, +-gx, +-gxy} (gkm: the set, 0 = not eligible)
+  int32_t gx = 0, gxy = 0, gkm = 0;
   // Diagonal-smoother epilogues (levels whose G is diagonal, jd = w g_ii^2,
   // vector precision): jmode 1 also writes Y2 = jd o Y (presmoothing of the
   // next level fused into its restriction); jmode 2 writes Y = X + jd o
@@ -183,6 +186,12 @@ void launch_spmm(ValType mt, VecType xt, VecType ot, const SpmmArgs& a, cudaStre
 void spmm_resolved_tile(VecType xt, VecType ot, const SpmmArgs& a, int* cpt, int* kl);
 // Whether launch_spmm runs the halo-staged kernel for these arguments.
 bool spmm_uses_halo(VecType xt, const SpmmArgs& a);
+// Whether launch_spmm runs the z-marching stencil kernel for these arguments.
+bool spmm_uses_stencil(ValType mt, VecType xt, VecType ot, const SpmmArgs& a);
+// The stencil form of a diagonal-offset matrix (offsets off[0..ndiag),
+// ascending): sets gx, gxy and the offset set gkm of `a` when they fit the
+// z-marching kernel's tiles (else leaves gkm = 0).
+void stencil_geometry(int32_t rows, int32_t ndiag, const int32_t* off, SpmmArgs& a);
 
 // Elementwise / transform / small kernels (k_misc.cu).
 void launch_transform_fwd(const double* b, int32_t nrhs, int64_t ld, const int32_t* perm, int64_t n_b,

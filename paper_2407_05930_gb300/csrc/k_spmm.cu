@@ -29,8 +29,10 @@
 #include <cuda_bf16.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "spmm_common.cuh"
+#include "stencil.cuh"
 
 namespace amgsym {
 
@@ -183,7 +185,8 @@ __global__ void __launch_bounds__(kBlock, 4) spmm_halo_kernel(SpmmArgs a) {
         }
       }
       if (live && e == 0)
-        row_epilogue<XT, OT, CT, DT, CPT, false, false>(a, row, c0, acc, Vec<XT, CPT>{}, false, dpart);
+        row_epilogue<XT, OT, CT, DT, CPT, false, false>(a, row, c0, acc, Vec<XT, CPT>{}, false, Vec<XT, CPT>{}, false,
+                                                        dpart);
     }
     __syncthreads();  // the next tile overwrites the halo
   }
@@ -284,8 +287,85 @@ static void launch_t(const SpmmArgs& a, cudaStream_t st) {
   }
 }
 
+void stencil_geometry(int32_t rows, int32_t ndiag, const int32_t* off, SpmmArgs& a) {
+  a.gx = a.gxy = a.gkm = 0;
+  if (ndiag <= 0 || rows <= 0) return;
+  int32_t s1 = 0, s2 = 0;  // the two distinct strides above 1
+  for (int d = 0; d < ndiag; ++d) {
+    const int32_t o = off[d] < 0 ? -off[d] : off[d];
+    if (o <= 1 || o == s1 || o == s2) continue;
+    if (!s1)
+      s1 = o;
+    else if (!s2)
+      s2 = o;
+    else
+      return;
+  }
+  if (!s1 || !s2) return;
+  const int32_t gx = std::min(s1, s2), gxy = std::max(s1, s2);
+  int km = 0;
+  for (int d = 0; d < ndiag; ++d) {
+    const int32_t o = off[d];
+    const int k = o == -gxy ? 0 : o == -gx ? 1 : o == -1 ? 2 : o == 0 ? 3 : o == 1 ? 4 : o == gx ? 5 : o == gxy ? 6 : -1;
+    if (k < 0) return;
+    km |= 1 << k;
+  }
+  if (km != kKindAll && km != kKindLower && km != kKindUpper) return;
+  if (gx % kZTX || gxy % gx || (gxy / gx) % kZTY || rows % gxy) return;
+  a.gx = gx;
+  a.gxy = gxy;
+  a.gkm = km;
+}
+
+bool spmm_uses_stencil(ValType mt, VecType xt, VecType ot, const SpmmArgs& a) {
+  // FP32 vectors, one thread per row with all 8 columns; the interface only
+  // with the full stencil (the reduced operator)
+  return a.ndiag > 0 && a.gkm != 0 && xt == VEC_F32 && ot == VEC_F32 && (mt == VAL_F32 || mt == VAL_BF16) &&
+         a.C == 8 && (!a.imask || a.gkm == kKindAll);
+}
+
+template <typename MT, typename XT, typename OT, int KM>
+static void launch_zk(const SpmmArgs& a, cudaStream_t st) {
+  const bool dot = a.dot.mode != DOT_NONE, ifc = a.imask != nullptr;
+  const size_t smem = stencil_smem_bytes(8, (int)sizeof(XT), dot);
+  const int64_t units = (int64_t)(a.gx / kZTX) * (a.gxy / a.gx / kZTY) * (a.rows / a.gxy);
+  count_launch();
+  // one wave of resident blocks, the (tile, plane) units split evenly
+  auto run = [&](auto kern) {
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>(resident_grid((const void*)kern, smem), units));
+    if (dot && (int64_t)g * a.C > a.dot.sc.partial_cap) g = (int)(a.dot.sc.partial_cap / a.C);
+    kern<<<g, kBlock, smem, st>>>(a);
+  };
+  if constexpr (KM == kKindAll) {
+    if (dot && ifc)
+      run(stencil_kernel<MT, XT, OT, 8, KM, true, true>);
+    else if (ifc)
+      run(stencil_kernel<MT, XT, OT, 8, KM, false, true>);
+    else if (dot)
+      run(stencil_kernel<MT, XT, OT, 8, KM, true, false>);
+    else
+      run(stencil_kernel<MT, XT, OT, 8, KM, false, false>);
+  } else {
+    if (dot)
+      run(stencil_kernel<MT, XT, OT, 8, KM, true, false>);
+    else
+      run(stencil_kernel<MT, XT, OT, 8, KM, false, false>);
+  }
+}
+
 template <typename MT, typename XT, typename OT>
 static void launch_c(const SpmmArgs& a, cudaStream_t st) {
+  if constexpr (std::is_same<XT, float>::value && std::is_same<OT, float>::value && !std::is_same<MT, double>::value) {
+    if (spmm_uses_stencil(std::is_same<MT, float>::value ? VAL_F32 : VAL_BF16, VEC_F32, VEC_F32, a)) {
+      if (a.gkm == kKindAll)
+        launch_zk<MT, XT, OT, kKindAll>(a, st);
+      else if (a.gkm == kKindLower)
+        launch_zk<MT, XT, OT, kKindLower>(a, st);
+      else
+        launch_zk<MT, XT, OT, kKindUpper>(a, st);
+      return;
+    }
+  }
   // V: elements of the narrower of X / Y in one 16-byte vector
   constexpr int V = 16 / (int)sizeof(XT) < 16 / (int)sizeof(OT) ? 16 / (int)sizeof(XT) : 16 / (int)sizeof(OT);
   const int want = a.cpt > 0 ? a.cpt : V;

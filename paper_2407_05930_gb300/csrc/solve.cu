@@ -135,7 +135,10 @@ static void run_spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecT
   int cpt = 0, kl = 0;
   spmm_resolved_tile(xt, ot, a, &cpt, &kl);
   const bool dot = a.dot.mode != DOT_NONE, ifc = a.imask != nullptr, dia = a.ndiag > 0;
-  const std::string kernel = std::string(spmm_uses_halo(xt, a) ? "spmm_halo_kernel<" : "spmm_kernel<") + tname(mt) + "," + tname(xt) + "," + tname(ot) + "," +
+  const char* kname = spmm_uses_stencil(mt, xt, ot, a) ? "stencil_kernel<"
+                      : spmm_uses_halo(xt, a)                ? "spmm_halo_kernel<"
+                                                             : "spmm_kernel<";
+  const std::string kernel = std::string(kname) + tname(mt) + "," + tname(xt) + "," + tname(ot) + "," +
                              std::to_string(cpt) + "," + std::to_string(kl) + "," + (dot ? "1" : "0") + "," +
                              (ifc ? "1" : "0") + "," + (dia ? "1" : "0") + ">";
   int level = -1;
@@ -321,6 +324,7 @@ void device_upload(amgsym_problem* p) {
   D->epoch = next_generation();
   CK(cudaGetDevice(&D->device_id));
   D->precisions = p->opts.precisions | 1;  // FP64 operator always (outer residuals)
+  D->zmarch = p->opts.zmarch != 0;
   D->nu = p->opts.nu;
   D->singular = p->singular;
   D->s = p->s;
@@ -576,6 +580,7 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
     }
     a.dval = M.dvals(mt);
     a.dstride = M.dstride;
+    if (c.D->zmarch) stencil_geometry(M.rows, M.ndiag, M.doff, a);
   }
   if (M.htiles > 0 && a.ndiag == 0) {
     a.htiles = M.htiles;
@@ -587,7 +592,10 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
   }
   if (dot) a.dot = *dot;
   a.skip = c.skip;
-  auto it = c.D->tiles.find(TileKey{M.idx, c.C, (int)mt, (int)xt, (int)ot});
+  // the dot-fused variant has its own tile where the tuner timed one
+  auto it = c.D->tiles.end();
+  if (dot) it = c.D->tiles.find(TileKey{M.idx, c.C, (int)mt, (int)xt, (int)ot, 1});
+  if (it == c.D->tiles.end()) it = c.D->tiles.find(TileKey{M.idx, c.C, (int)mt, (int)xt, (int)ot, 0});
   if (it != c.D->tiles.end()) {
     a.kl = it->second.kl;
     a.cpt = it->second.cpt;
@@ -611,7 +619,10 @@ void spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecType ot, con
 // candidate tile -- columns per thread (one or two 16-byte vectors) times
 // entry lanes per row (1..16) -- with CUDA events and keep the fastest.  It
 // runs once per (C, precision) before the PCG graph is captured, on scratch
-// level vectors (their contents do not matter for timing).  Results are
+// level vectors (their contents do not matter for timing).  The dot-fused
+// products of the PCG iteration (q = A^ p with <p, q>; the last finest-level
+// smoother update with <r, z>) are timed as their own variant, since their
+// register budget differs from the plain product's.  Results are
 // bit-reproducible for a fixed tile choice; the choice itself is timing-based.
 void tune_tiles(const Ctx& c) {
   Device* D = c.D;
@@ -627,22 +638,31 @@ void tune_tiles(const Ctx& c) {
     if (W.lw[l].z) CK(cudaMemsetAsync(W.lw[l].z, 0, es * (size_t)D->lv[l].n * c.C, c.st));
     if (W.lw[l].r) CK(cudaMemsetAsync(W.lw[l].r, 0, es * (size_t)D->lv[l].n * c.C, c.st));
   }
+  // dot: the fused-dot variant of the product (with its epilogue operand),
+  // timed and stored as its own tile (variant 1): its register budget differs
   struct Job {
     const DevCsr* M;
     ValType mt;
     const void* X;
     void* Y;
     bool iface;
+    bool dot = false;
+    double beta = 0.0;
+    const void* W = nullptr;
   };
   std::vector<Job> jobs;
   const ValType kmt = c.vt == VEC_F64 ? VAL_F64 : VAL_F32;
   jobs.push_back({&D->Ainn, kmt, W.lw[0].t, W.lw[0].r, true});  // reduced operator
+  // the PCG's q = A^ p with <p, q>
+  jobs.push_back({&D->Ainn, kmt, W.lw[0].t, W.lw[0].r, true, true, 0.0, W.lw[0].t});
   for (size_t l = 0; l + 1 < D->lv.size(); ++l) {
     const DevLevel& L = D->lv[l];
     if (L.cinv) break;
     jobs.push_back({&L.A, c.mt, W.lw[l].t, W.lw[l].r, false});
     jobs.push_back({&L.G, c.mt, W.lw[l].t, W.lw[l].r, false});
     jobs.push_back({&L.Gt, c.mt, W.lw[l].t, W.lw[l].r, false});
+    // the last finest-level smoother update z += w G^T (...) with <r, z>
+    if (l == 0) jobs.push_back({&L.Gt, c.mt, W.lw[l].t, W.lw[l].r, false, true, 1.0, W.lw[l].z});
     jobs.push_back({&L.R, c.mt, W.lw[l].r, W.lw[l + 1].y, false});
     jobs.push_back({&L.P, c.mt, W.lw[l + 1].z, W.lw[l].t, false});
   }
@@ -658,11 +678,19 @@ void tune_tiles(const Ctx& c) {
       for (int kl = 1; kl <= 16; kl *= 2) {
         if (kl > 1 && ((tpc & (tpc - 1)) || tpc * kl > 32 || j.M->ndiag > 0)) break;
         Ctx cc = c;
-        D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)c.vt}] = Tile{cpt, kl};
-        spmm(cc, *j.M, j.mt, c.vt, c.vt, j.X, j.Y, 1.0, 0.0, nullptr, j.iface, nullptr);  // warm-up
+        const int var = j.dot ? 1 : 0;
+        D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)c.vt, var}] = Tile{cpt, kl};
+        DotArgs dj;  // per-column sums only (no finalisation), on the solve's scratch partials
+        dj.mode = DOT_WY;
+        dj.final = FIN_NONE;
+        dj.W = j.W;
+        dj.sc = D->sc_out;
+        const DotArgs* dp = j.dot ? &dj : nullptr;
+        const void* Zj = j.beta != 0.0 ? j.Y : nullptr;
+        spmm(cc, *j.M, j.mt, c.vt, c.vt, j.X, j.Y, 1.0, j.beta, Zj, j.iface, dp);  // warm-up
         CK(cudaEventRecord(e0, c.st));
         const int reps = 3;
-        for (int r = 0; r < reps; ++r) spmm(cc, *j.M, j.mt, c.vt, c.vt, j.X, j.Y, 1.0, 0.0, nullptr, j.iface, nullptr);
+        for (int r = 0; r < reps; ++r) spmm(cc, *j.M, j.mt, c.vt, c.vt, j.X, j.Y, 1.0, j.beta, Zj, j.iface, dp);
         CK(cudaEventRecord(e1, c.st));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -674,9 +702,10 @@ void tune_tiles(const Ctx& c) {
       }
     }
     if (best.cpt > 0) {
-      // the same tile serves every output type / fused variant of this matrix
-      D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)c.vt}] = best;
-      D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)VEC_F32}] = best;
+      // the same tile serves every output type of this matrix and variant
+      const int var = j.dot ? 1 : 0;
+      D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)c.vt, var}] = best;
+      D->tiles[TileKey{j.M->idx, c.C, (int)j.mt, (int)c.vt, (int)VEC_F32, var}] = best;
     }
   }
   cudaEventDestroy(e0);

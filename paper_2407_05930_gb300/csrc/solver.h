@@ -73,7 +73,8 @@ struct GraphCache {
 struct Tile {
   int cpt = 0, kl = 0;
 };
-using TileKey = std::tuple<const void*, int32_t, int, int, int>;  // matrix idx array, C, mt, xt, ot
+// matrix idx array, C, mt, xt, ot, variant (0: plain epilogue, 1: with the fused dot)
+using TileKey = std::tuple<const void*, int32_t, int, int, int, int>;
 
 // Generations come from one process-wide counter that only goes up, so a
 // value identifies one Device object and one set of its work arrays for the
@@ -140,6 +141,7 @@ struct Device {
   double* lrc_V = nullptr;
   std::vector<double> lrc_theta;
   bool has_amgr = false;
+  bool zmarch = false;  // opts.zmarch: finest-level diagonal-offset products as the z-marching stencil
   DevAmgr amgr;
   // Low-rank correction of LRCFSAI(k) (eq. "LRCFSAI"), per block: Z = G_inn^T V
   // (V the k eigenvectors of G_inn A^_i G_inn^T of the smallest eigenvalues)

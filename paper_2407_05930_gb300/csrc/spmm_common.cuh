@@ -264,7 +264,8 @@ __device__ __forceinline__ int flag_index(const SpmmArgs& a, int row) {
 // Epilogue of one row (entry lane 0): Y = alpha acc + beta Z, the optional dot.
 template <typename XT, typename OT, typename CT, typename DT, int CPT, bool HAS_DOT, bool COH>
 __device__ __forceinline__ void row_epilogue(const SpmmArgs& a, int row, int c0, CT (&acc)[CPT],
-                                             const Vec<XT, CPT>& zpre, bool use_zpre, DT (&dpart)[CPT]) {
+                                             const Vec<XT, CPT>& zpre, bool use_zpre, const Vec<XT, CPT>& wpre,
+                                             bool use_wpre, DT (&dpart)[CPT]) {
   const int C = a.C;
   const CT alpha = (CT)a.alpha, beta = (CT)a.beta;
   // Y may alias Z (in-place update z += ...); each row reads Z before writing Y.
@@ -306,7 +307,9 @@ __device__ __forceinline__ void row_epilogue(const SpmmArgs& a, int row, int c0,
   stv<OT, CPT>(Y + (int64_t)row * C + c0, out);
   if (HAS_DOT) {
     if (a.dot.mode == DOT_WY) {
-      const Vec<XT, CPT> wv = ldx<XT, CPT, COH>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
+      // the dot partner as loaded early by the caller (use_wpre), else now
+      const Vec<XT, CPT> wv =
+          use_wpre ? wpre : ldx<XT, CPT, COH>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
 #pragma unroll
       for (int q = 0; q < CPT; ++q) dpart[q] = fma((DT)wv.v[q], (DT)acc[q], dpart[q]);
     } else {
@@ -344,9 +347,12 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
   static_assert(!DIA || KL == 1, "the diagonal-offset form runs one entry lane per row");
   using CT = typename ComputeOf<MT, XT>::type;
   using DT = typename AccOf<XT>::type;  // per-thread dot partial type
-  // Early epilogue-operand load only where the register budget allows it
-  // without spills (the variants launched at 6 blocks per SM).
+  // Early epilogue-operand loads, issued with the row's matrix and X loads so
+  // that the epilogue adds no dependent round trip: Z (beta != 0) in the CSR
+  // variants launched at 6 blocks per SM, Z and the dot partner W in the
+  // diagonal-form dot variants (3 blocks per SM, registers to spare).
   constexpr bool ZPF = (HAS_DOT || HAS_IFACE) && !DIA;
+  constexpr bool DPF = HAS_DOT && DIA;
   constexpr bool PTR_PF = ZPF && !DIA;
   const int C = a.C;
   const int TPC = C / CPT;
@@ -388,7 +394,7 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
     CT acc[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) acc[q] = (CT)0;
-    Vec<XT, CPT> zpre;
+    Vec<XT, CPT> zpre, wpre;
     int kb = kb_next, ke = ke_next;
     if (PTR_PF) {
       if (slot_ok && row + step_rows < row_end) {
@@ -404,7 +410,9 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
       // interface flag word and epilogue operand loaded with the row pointers,
       // off the critical path of the gathers
       const uint32_t iface_word = (HAS_IFACE && e == 0) ? __ldg(a.imask + (row >> 5)) : 0u;
-      if (ZPF && e == 0 && a.beta != 0.0) zpre = ldx<XT, CPT, COH>(Z + (int64_t)row * C + c0);
+      if ((ZPF || DPF) && e == 0 && a.beta != 0.0) zpre = ldx<XT, CPT, COH>(Z + (int64_t)row * C + c0);
+      if (DPF && e == 0 && a.dot.mode == DOT_WY)
+        wpre = ldx<XT, CPT, COH>(static_cast<const XT*>(a.dot.W) + (int64_t)row * C + c0);
       if (DIA)
         dia_row<MT, XT, CT, CPT, COH>(a, row, c0, acc);
       else
@@ -413,8 +421,8 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
     }
     lanes(acc);
     if (live && e == 0 && !flagged)
-      row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, zpre, ZPF && a.beta != 0.0,
-                                                      dpart);
+      row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, zpre, (ZPF || DPF) && a.beta != 0.0, wpre,
+                                                      DPF && a.dot.mode == DOT_WY, dpart);
   }
   if (HAS_IFACE) {
     // the flagged rows, with their couplings
@@ -437,7 +445,9 @@ __device__ __forceinline__ void spmm_tile(const SpmmArgs& a, int first_slot, int
         if (e == 0) iface_row<XT, CT, CPT, COH>(a, f, c0, acc);
       }
       lanes(acc);
-      if (live && e == 0) row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, Vec<XT, CPT>{}, false, dpart);
+      if (live && e == 0)
+        row_epilogue<XT, OT, CT, DT, CPT, HAS_DOT, COH>(a, row, c0, acc, Vec<XT, CPT>{}, false, Vec<XT, CPT>{}, false,
+                                                        dpart);
     }
   }
 }
