@@ -158,6 +158,24 @@ typedef struct {
                                and waits one round trip and a barrier per plane; the
                                diagonal-offset kernel keeps as many rows in flight without
                                barriers), 71.1 ms a solve against 67.4 ms */
+  int32_t sell;             /* 1: the CSR matrices of the hierarchy (A_l, R_l, G_l with 8 or
+                               more entries per row on average, not in the diagonal-offset
+                               form) are also stored sliced
+                               (SELL-32: rows sorted by length within windows of 256 rows,
+                               slices of 32 rows, each row's entries in their CSR order,
+                               column-major in the slice), and a product without a dot or
+                               interface at one vector of C columns per thread (8 FP32
+                               columns) runs one row per lane on it: every lane of a warp
+                               loads its next entries' columns in one coalesced load and keeps
+                               its gathers in flight, instead of 8 rows per warp each walking
+                               row pointer -> column -> gather chains.  Each row keeps the CSR
+                               kernel's entry-lane partial sums and their combination order, so
+                               the products are bit-identical to the CSR kernel.  Costs about
+                               1.1x the CSR index and value arrays.  0 (default) = CSR only: at
+                               256^3 the level-1 residual took 100 us sliced against 72 us CSR
+                               (a 256-row warp-pair covers scattered rows; the CSR kernel's 8
+                               neighbouring rows per warp share their gathers), 90 ms a mixed
+                               solve against 67; the FP64 solve ran 254 ms against 282 */
 } amgsym_opts;
 
 #define AMGSYM_MAX_DIAG 8

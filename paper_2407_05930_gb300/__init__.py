@@ -74,6 +74,7 @@ class Opts(ctypes.Structure):
         ("amgr_distance", ctypes.c_int32),
         ("amgr_interp_max", ctypes.c_int32),
         ("zmarch", ctypes.c_int32),
+        ("sell", ctypes.c_int32),
     ]
 
 

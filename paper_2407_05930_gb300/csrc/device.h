@@ -51,7 +51,25 @@ struct DevCsr {
   int32_t* hptr = nullptr;
   int32_t* hx = nullptr;
   uint16_t* lidx = nullptr;
+  // Sliced form (nslices > 0; SELL-32 with windowed row sorting): slice s
+  // holds the rows srow[32 s .. 32 s + 32) (-1: none), each row's entries in
+  // its CSR order, column-major: entry e of slot l at sptr[s] + 32 e + l
+  // (sidx -1 past the row's end).  Rows are sorted by length, longest first,
+  // within windows of kSellWindow rows, so a slice's width is close to its
+  // rows' lengths.  One value array per precision built.
+  int32_t nslices = 0;
+  int64_t sentries = 0;
+  int32_t* sptr = nullptr;
+  int32_t* srow = nullptr;
+  int32_t* sidx = nullptr;
+  double* sv64 = nullptr;
+  float* sv32 = nullptr;
+  __nv_bfloat16* sv16 = nullptr;
+  const void* svals(ValType t) const {
+    return t == VAL_F64 ? (const void*)sv64 : t == VAL_F32 ? (const void*)sv32 : (const void*)sv16;
+  }
 };
+constexpr int kSellWindow = 256;
 
 // Interface couplings A_out,i of eq. "hL_splitting" in a form the SpMM can
 // look up per row at ~0.25 byte per row: a bit per row (is there any
@@ -177,6 +195,14 @@ struct SpmmArgs {
   const int32_t* hptr = nullptr;
   const int32_t* hx = nullptr;
   const uint16_t* lidx = nullptr;
+  // Sliced form of a CSR matrix (nslices > 0; see DevCsr): used by
+  // launch_spmm for products without a dot or interface at one vector of C
+  // columns per thread with at most 4 entry lanes, else the CSR kernel runs.
+  int32_t nslices = 0;
+  const int32_t* sptr = nullptr;
+  const int32_t* srow = nullptr;
+  const int32_t* sidx = nullptr;
+  const void* sval = nullptr;
   DotArgs dot;
 };
 
@@ -186,6 +212,8 @@ void launch_spmm(ValType mt, VecType xt, VecType ot, const SpmmArgs& a, cudaStre
 void spmm_resolved_tile(VecType xt, VecType ot, const SpmmArgs& a, int* cpt, int* kl);
 // Whether launch_spmm runs the halo-staged kernel for these arguments.
 bool spmm_uses_halo(VecType xt, const SpmmArgs& a);
+// Whether launch_spmm runs the sliced (SELL) kernel for these arguments.
+bool spmm_uses_sell(VecType xt, VecType ot, const SpmmArgs& a);
 // Whether launch_spmm runs the z-marching stencil kernel for these arguments.
 bool spmm_uses_stencil(ValType mt, VecType xt, VecType ot, const SpmmArgs& a);
 // The stencil form of a diagonal-offset matrix (offsets off[0..ndiag),

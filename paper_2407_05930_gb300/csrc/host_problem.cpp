@@ -67,6 +67,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->amgr_distance = 1;
   o->amgr_interp_max = 4;
   o->zmarch = 0;
+  o->sell = 0;
 }
 
 extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {

@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "spmm_common.cuh"
+#include "sell.cuh"
 #include "stencil.cuh"
 
 namespace amgsym {
@@ -257,6 +258,25 @@ static void launch_k(const SpmmArgs& a, cudaStream_t st) {
   }
 }
 
+// One warp per (slice, part): C / (16-byte vector) lanes per row.
+template <typename XT>
+static bool sell_lanes_ok(int32_t C) {
+  constexpr int v = 16 / (int)sizeof(XT);
+  if (C % v) return false;
+  const int tpc = C / v;
+  return tpc >= 1 && tpc <= 32 && (tpc & (tpc - 1)) == 0;
+}
+
+template <typename MT, typename XT, typename OT, int KL>
+static void launch_s(const SpmmArgs& a, cudaStream_t st) {
+  auto kern = sell_kernel<MT, XT, OT, KL>;
+  count_launch();
+  const int64_t tasks = (int64_t)a.nslices * (a.C / (16 / (int)sizeof(XT)));
+  const int64_t g = std::max<int64_t>(1, (tasks + kBlock / 32 - 1) / (kBlock / 32));
+  if (g > INT32_MAX) fail(AMGSYM_ERR_ARG, "sliced product too large for one launch");
+  kern<<<(unsigned)g, kBlock, 0, st>>>(a);
+}
+
 template <typename MT, typename XT, typename OT, int CPT>
 static void launch_t(const SpmmArgs& a, cudaStream_t st) {
   if (a.ndiag > 0) {  // diagonal-offset form: one lane per row
@@ -276,6 +296,15 @@ static void launch_t(const SpmmArgs& a, cudaStream_t st) {
       case 8: launch_h<MT, XT, OT, CPT, 8>(a, st); break;
       default: launch_h<MT, XT, OT, CPT, 16>(a, st); break;
     }
+    return;
+  }
+  if (a.nslices > 0 && a.dot.mode == DOT_NONE && !a.imask && kl <= 4 && sell_lanes_ok<XT>(a.C)) {
+    if (kl == 1)
+      launch_s<MT, XT, OT, 1>(a, st);
+    else if (kl == 2)
+      launch_s<MT, XT, OT, 2>(a, st);
+    else
+      launch_s<MT, XT, OT, 4>(a, st);
     return;
   }
   switch (kl) {
@@ -315,6 +344,13 @@ void stencil_geometry(int32_t rows, int32_t ndiag, const int32_t* off, SpmmArgs&
   a.gx = gx;
   a.gxy = gxy;
   a.gkm = km;
+}
+
+bool spmm_uses_sell(VecType xt, VecType ot, const SpmmArgs& a) {
+  if (a.nslices <= 0 || a.ndiag > 0 || a.dot.mode != DOT_NONE || a.imask || spmm_uses_halo(xt, a)) return false;
+  int cpt = 0, kl = 0;
+  spmm_resolved_tile(xt, ot, a, &cpt, &kl);
+  return kl <= 4 && (xt == VEC_F64 ? sell_lanes_ok<double>(a.C) : sell_lanes_ok<float>(a.C));
 }
 
 bool spmm_uses_stencil(ValType mt, VecType xt, VecType ot, const SpmmArgs& a) {

@@ -137,6 +137,7 @@ static void run_spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecT
   const bool dot = a.dot.mode != DOT_NONE, ifc = a.imask != nullptr, dia = a.ndiag > 0;
   const char* kname = spmm_uses_stencil(mt, xt, ot, a) ? "stencil_kernel<"
                       : spmm_uses_halo(xt, a)                ? "spmm_halo_kernel<"
+                      : spmm_uses_sell(xt, ot, a)            ? "sell_kernel<"
                                                              : "spmm_kernel<";
   const std::string kernel = std::string(kname) + tname(mt) + "," + tname(xt) + "," + tname(ot) + "," +
                              std::to_string(cpt) + "," + std::to_string(kl) + "," + (dot ? "1" : "0") + "," +
@@ -225,8 +226,56 @@ static bool build_halo(const Csr& M, int64_t budget_bytes, HostHalo& H) {
   return false;
 }
 
+// Sliced form (SELL-32) of a CSR matrix, see DevCsr: rows sorted by length
+// (longest first, stable) within windows of kSellWindow rows, then cut into
+// slices of 32; false when the padded entries would not fit 32-bit offsets.
+struct HostSell {
+  std::vector<int32_t> sptr, srow, sidx;
+  std::vector<int64_t> src;  // CSR entry of each slot, -1 for padding
+};
+
+static bool build_sell(const Csr& M, HostSell& S) {
+  const int64_t n = M.rows;
+  if (n <= 0) return false;
+  std::vector<int32_t> order((size_t)n);
+  for (int64_t i = 0; i < n; ++i) order[i] = (int32_t)i;
+  auto len = [&](int32_t r) { return M.ptr[r + 1] - M.ptr[r]; };
+  for (int64_t w0 = 0; w0 < n; w0 += kSellWindow) {
+    const int64_t w1 = std::min<int64_t>(n, w0 + kSellWindow);
+    std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int32_t a, int32_t b) { return len(a) > len(b); });
+  }
+  const int64_t ns = (n + 31) / 32;
+  S.sptr.assign((size_t)ns + 1, 0);
+  S.srow.assign((size_t)ns * 32, -1);
+  int64_t total = 0;
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t width = 0;
+    for (int l = 0; l < 32 && s * 32 + l < n; ++l) {
+      const int32_t r = order[s * 32 + l];
+      S.srow[s * 32 + l] = r;
+      width = std::max<int64_t>(width, len(r));
+    }
+    total += width * 32;
+    if (total > INT32_MAX) return false;
+    S.sptr[s + 1] = (int32_t)total;
+  }
+  S.sidx.assign((size_t)total, -1);
+  S.src.assign((size_t)total, -1);
+  for (int64_t s = 0; s < ns; ++s)
+    for (int l = 0; l < 32; ++l) {
+      const int32_t r = S.srow[s * 32 + l];
+      if (r < 0) continue;
+      for (int64_t e = 0; e < len(r); ++e) {
+        const int64_t pos = S.sptr[s] + e * 32 + l;
+        S.sidx[pos] = M.idx[M.ptr[r] + e];
+        S.src[pos] = M.ptr[r] + e;
+      }
+    }
+  return true;
+}
+
 static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions, const Dia* dia = nullptr,
-                         int halo_kb = 0) {
+                         int halo_kb = 0, bool sell = false) {
   DevCsr D;
   if (M.rows > INT32_MAX || M.nnz() > INT32_MAX) fail(AMGSYM_ERR_ARG, "matrix too large for 32-bit device indices");
   D.rows = (int32_t)M.rows;
@@ -283,6 +332,29 @@ static DevCsr upload_csr(std::vector<void*>& owner, const Csr& M, int precisions
     D.hptr = upload(owner, H.hptr.data(), (int64_t)H.hptr.size());
     D.hx = upload(owner, H.hx.data(), (int64_t)H.hx.size());
     D.lidx = upload(owner, H.lidx.data(), (int64_t)H.lidx.size());
+  }
+  HostSell S;
+  // rows of a few entries (prolongations: 1-3) ran at half the CSR speed sliced
+  if (D.ndiag == 0 && sell && M.nnz() >= 8 * M.rows && build_sell(M, S)) {
+    // the same value conversions as the CSR copies (padding: 0)
+    D.nslices = (int32_t)(S.sptr.size() - 1);
+    D.sentries = (int64_t)S.sidx.size();
+    D.sptr = upload(owner, S.sptr.data(), (int64_t)S.sptr.size());
+    D.srow = upload(owner, S.srow.data(), (int64_t)S.srow.size());
+    D.sidx = upload(owner, S.sidx.data(), D.sentries);
+    std::vector<double> v((size_t)D.sentries, 0.0);
+    for (int64_t q = 0; q < D.sentries; ++q)
+      if (S.src[q] >= 0) v[q] = M.val[S.src[q]];
+    if (precisions & 1) D.sv64 = upload(owner, v.data(), D.sentries);
+    if (precisions & 2) {
+      std::vector<float> f(v.begin(), v.end());
+      D.sv32 = upload(owner, f.data(), D.sentries);
+    }
+    if (precisions & 4) {
+      std::vector<__nv_bfloat16> h((size_t)D.sentries);
+      for (int64_t q = 0; q < D.sentries; ++q) h[q] = __float2bfloat16((float)v[q]);
+      D.sv16 = upload(owner, h.data(), D.sentries);
+    }
   }
   return D;
 }
@@ -341,14 +413,15 @@ void device_upload(amgsym_problem* p) {
     V.omega = L.omega;
     // level 0 keeps FP64 always (the reduced operator of the outer loop)
     const int hkb = p->opts.halo_kb;
-    V.A = upload_csr(D->owned, L.A, l == 0 ? D->precisions : p->opts.precisions, &L.Adia, hkb);
+    const bool sl = p->opts.sell != 0;
+    V.A = upload_csr(D->owned, L.A, l == 0 ? D->precisions : p->opts.precisions, &L.Adia, hkb, sl);
     if (!L.coarse_inv.empty()) {
       V.cinv = upload(D->owned, L.coarse_inv.data(), (int64_t)L.coarse_inv.size());
     } else {
-      V.P = upload_csr(D->owned, L.P, p->opts.precisions, nullptr, hkb);
-      V.R = upload_csr(D->owned, L.R, p->opts.precisions, nullptr, hkb);
-      V.G = upload_csr(D->owned, L.G, p->opts.precisions, &L.Gdia, hkb);
-      V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions, &L.Gtdia, hkb);
+      V.P = upload_csr(D->owned, L.P, p->opts.precisions, nullptr, hkb, sl);
+      V.R = upload_csr(D->owned, L.R, p->opts.precisions, nullptr, hkb, sl);
+      V.G = upload_csr(D->owned, L.G, p->opts.precisions, &L.Gdia, hkb, sl);
+      V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions, &L.Gtdia, hkb, sl);
       // a diagonal FSAI factor: the smoother is the diagonal omega g_ii^2
       bool diag = L.G.nnz() == L.G.rows;
       for (int64_t i = 0; diag && i < L.G.rows; ++i) diag = L.G.idx[L.G.ptr[i]] == (int32_t)i;
@@ -581,6 +654,13 @@ SpmmArgs make_spmm_args(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, V
     a.dval = M.dvals(mt);
     a.dstride = M.dstride;
     if (c.D->zmarch) stencil_geometry(M.rows, M.ndiag, M.doff, a);
+  }
+  if (M.nslices > 0 && a.ndiag == 0 && M.svals(mt)) {
+    a.nslices = M.nslices;
+    a.sptr = M.sptr;
+    a.srow = M.srow;
+    a.sidx = M.sidx;
+    a.sval = M.svals(mt);
   }
   if (M.htiles > 0 && a.ndiag == 0) {
     a.htiles = M.htiles;

@@ -23,8 +23,9 @@ DEV = "cuda"
 
 def _pair(N, s, **kw):
     g = gaussian_logk(N, s, seed=14, corr=3.0)
-    P = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=64, precisions=7, halo_kb=64, **kw)
-    Q = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=64, precisions=7, halo_kb=0, **kw)
+    # the CSR kernel as the comparison (sell=0): tuned solves then time the same candidates
+    P = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=64, precisions=7, halo_kb=64, sell=0, **kw)
+    Q = amg.Problem.structured(N, 1.5, g, s).setup(coarse_max=64, precisions=7, halo_kb=0, sell=0, **kw)
     return P, Q
 
 
