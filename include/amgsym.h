@@ -446,7 +446,10 @@ amgsym_status amgsym_vcycle(amgsym_t h, const void* R_dev, void* Z_dev, int32_t 
  * the paper: it reports how this library's kernels spend a step of Alg. 1).
  *
  * Runs, on `stream`, the launches of one step of amgsym_solve with precision
- * `prec` (and finest_hat) on b_dev (device FP64 natural order [nrhs][ld]):
+ * `prec`, finest_hat and `preconditioner` (AMGSYM_PC_AMG, or AMGSYM_PC_AMGR
+ * after a setup with opts.amgr: the PCG start and iteration then apply AMGR,
+ * whose coarse AMG launches are records too) on b_dev (device FP64 natural
+ * order [nrhs][ld]):
  * the forward transform, the FP64 outer residual, in the mixed modes the
  * inner reference norm, the PCG start (one V-cycle and z -> p), ONE PCG
  * iteration (reduced SpMM with <p, q>, the x/r update with <r, r>, the
@@ -475,8 +478,8 @@ typedef struct {
   double us;
 } amgsym_prof_record;
 amgsym_status amgsym_profile_step(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs, int64_t ld,
-                                  int32_t prec, int32_t finest_hat, void* stream, amgsym_prof_record* out,
-                                  int32_t max_records, int32_t* count);
+                                  int32_t prec, int32_t finest_hat, int32_t preconditioner, void* stream,
+                                  amgsym_prof_record* out, int32_t max_records, int32_t* count);
 
 /* AMGR (Sec. 3.2), built by amgsym_setup with opts->amgr = 1.
  *

@@ -140,7 +140,7 @@ def _load():
         "amgsym_get_level_matrix": (i32, [P, i32, i32, pi64, pi32, pdbl]),
         "amgsym_level_dia": (i32, [P, i32, i32, pi32, pi32, pi32]),
         "amgsym_cycle_timeout_check": (i32, [P, i32, i32, P]),
-        "amgsym_profile_step": (i32, [P, P, P, i32, i64, i32, i32, P, ctypes.POINTER(ProfRecord), i32, pi32]),
+        "amgsym_profile_step": (i32, [P, P, P, i32, i64, i32, i32, i32, P, ctypes.POINTER(ProfRecord), i32, pi32]),
         "amgsym_solve": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
         "amgsym_solve_adjoint": (i32, [P, P, P, i32, i64, ctypes.POINTER(SolveOpts), P, ctypes.POINTER(SolveInfo)]),
         "amgsym_transform_forward": (i32, [P, P, i32, i64, P, P]),
@@ -585,13 +585,14 @@ class Problem:
         return Z
 
     def profile_step(self, b, x, nrhs: int, prec: int = PREC_MIXED_FP32, finest_hat: bool = False,
-                     max_records: int = 512):
+                     max_records: int = 512, preconditioner: int = PC_AMG):
         """Event-timed launches of one solve step (amgsym_profile_step): a list of
         dicts with kernel, role, level, phase (1 = every PCG iteration), bytes, us."""
         recs = (ProfRecord * max_records)()
         cnt = ctypes.c_int32()
         _check(lib.amgsym_profile_step(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs,
-                                       self.n, prec, 1 if finest_hat else 0, self._stream(), recs, max_records,
+                                       self.n, prec, 1 if finest_hat else 0, int(preconditioner), self._stream(),
+                                       recs, max_records,
                                        ctypes.byref(cnt)))
         return [dict(kernel=r.kernel.decode(), role=r.role.decode(), level=r.level, phase=r.phase, bytes=r.bytes,
                      us=r.us) for r in recs[: min(cnt.value, max_records)]]

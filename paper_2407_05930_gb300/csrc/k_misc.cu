@@ -404,34 +404,67 @@ void launch_zero(VecType vt, int64_t count, void* dst, cudaStream_t st) {
     zero_kernel<float><<<g, kBlock, 0, st>>>(count, static_cast<float*>(dst));
 }
 
-template <typename T>
+// Per-column dots of two [rows][C] vectors.  A thread owns CPT consecutive
+// columns (one 16-byte vector where C allows) of its row slots and sums their
+// products in the vector precision (DotAcc: FP32 for FP32 vectors, as the
+// fused dots of the SpMM epilogues; the FP64 rate of this GPU is a small
+// fraction of its FP32 rate), then the block and grid combine the per-thread
+// partials in FP64 in a fixed order.
+template <typename T, int CPT>
 __global__ void __launch_bounds__(kBlock) dot_kernel(int64_t rows, int32_t C, const T* __restrict__ a,
                                                      const T* __restrict__ b, DotArgs dot, const int32_t* skip) {
+  using DT = typename DotAcc<T>::type;
+  using V = VecM<T, CPT>;
   if (skip && *skip == 0) return;
-  const int TPR = C;
+  const int TPR = C / CPT;
   const int rows_pb = kBlock / TPR;
   const int rloc = threadIdx.x / TPR;
-  const int c0 = threadIdx.x % TPR;
+  const int c0 = (threadIdx.x % TPR) * CPT;
   const bool has_cols = rloc < rows_pb;
-  double part[1] = {0.0};
+  DT acc[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) acc[k] = (DT)0;
   if (has_cols)
-    for (int64_t row = blockIdx.x * (int64_t)rows_pb + rloc; row < rows; row += (int64_t)gridDim.x * rows_pb)
-      part[0] += (double)a[row * C + c0] * (double)b[row * C + c0];
+    for (int64_t row = blockIdx.x * (int64_t)rows_pb + rloc; row < rows; row += (int64_t)gridDim.x * rows_pb) {
+      const V av = *reinterpret_cast<const V*>(a + row * C + c0);
+      const V bv = *reinterpret_cast<const V*>(b + row * C + c0);
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) acc[k] = fma((DT)av.v[k], (DT)bv.v[k], acc[k]);
+    }
+  double part[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) part[k] = has_cols ? (double)acc[k] : 0.0;
   extern __shared__ double sm[];
-  block_dot<1>(dot, part, c0, has_cols, rloc, rows_pb, TPR, C, sm, blockIdx.x, gridDim.x, dot.sc.partials,
-               dot.sc.ticket);
+  block_dot<CPT>(dot, part, c0, has_cols, rloc, rows_pb, TPR, C, sm, blockIdx.x, gridDim.x, dot.sc.partials,
+                 dot.sc.ticket);
+}
+
+template <typename T, int CPT>
+static void dot_c(int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot, cudaStream_t st,
+                  const int32_t* skip) {
+  const int TPR = C / CPT, rows_pb = kBlock / TPR;
+  int g = grid_for(rows, rows_pb > 0 ? rows_pb : 1);
+  if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
+  const size_t smem = sizeof(double) * (size_t)dot_smem_doubles(TPR, rows_pb, C);
+  dot_kernel<T, CPT><<<g, kBlock, smem, st>>>(rows, C, static_cast<const T*>(a), static_cast<const T*>(b), dot, skip);
 }
 
 void launch_dot(VecType vt, int64_t rows, int32_t C, const void* a, const void* b, const DotArgs& dot,
                 cudaStream_t st, const int32_t* skip) {
   count_launch();
-  int g = grid_for(rows, kBlock / C > 0 ? kBlock / C : 1);
-  if ((int64_t)g * C > dot.sc.partial_cap) g = (int)(dot.sc.partial_cap / C);
-  const size_t smem = sizeof(double) * (size_t)dot_smem_doubles(C, kBlock / C, C);
-  if (vt == VEC_F64)
-    dot_kernel<double><<<g, kBlock, smem, st>>>(rows, C, static_cast<const double*>(a), static_cast<const double*>(b), dot, skip);
-  else
-    dot_kernel<float><<<g, kBlock, smem, st>>>(rows, C, static_cast<const float*>(a), static_cast<const float*>(b), dot, skip);
+  if (vt == VEC_F64) {
+    if (C % 2 == 0)
+      dot_c<double, 2>(rows, C, a, b, dot, st, skip);
+    else
+      dot_c<double, 1>(rows, C, a, b, dot, st, skip);
+  } else {
+    if (C % 4 == 0)
+      dot_c<float, 4>(rows, C, a, b, dot, st, skip);
+    else if (C % 2 == 0)
+      dot_c<float, 2>(rows, C, a, b, dot, st, skip);
+    else
+      dot_c<float, 1>(rows, C, a, b, dot, st, skip);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -1641,7 +1641,8 @@ void profile_step_body(Device* D, amgsym_t h, const double* b_dev, double* x_dev
   }
   // PCG start: z = M r with <r, z>, p = z
   DotArgs drz = make_dot(sc, DOT_WY, FIN_STORE_RZ, W.r, nrhs, D->nb, 0.0, 0);
-  vcycle(c, 0, W.r, W.z, &drz);
+  drz.coupled = c.pc == AMGSYM_PC_AMGR;
+  precondition(c, W.r, W.z, &drz);
   timed(std::string("copy_kernel<") + tname(vt) + ">", "p = z", 2 * xsize(vt) * n_b * C,
         [&] { launch_copy(vt, n_b * C, W.p, W.z, st); });
   prof.phase = 1;
@@ -1657,8 +1658,9 @@ void profile_step_body(Device* D, amgsym_t h, const double* b_dev, double* x_dev
 }  // namespace
 
 extern "C" amgsym_status amgsym_profile_step(amgsym_t h, const double* b_dev, double* x_dev, int32_t nrhs,
-                                             int64_t ld, int32_t prec, int32_t finest_hat, void* stream,
-                                             amgsym_prof_record* out, int32_t max_records, int32_t* count) {
+                                             int64_t ld, int32_t prec, int32_t finest_hat, int32_t preconditioner,
+                                             void* stream, amgsym_prof_record* out, int32_t max_records,
+                                             int32_t* count) {
   API_BEGIN
   Device* D = require_dev(h);
   if (nrhs < 1 || (int64_t)nrhs * D->nb > 256) fail(AMGSYM_ERR_ARG, "nrhs * 2^s must be in [1, 256]");
@@ -1672,7 +1674,12 @@ extern "C" amgsym_status amgsym_profile_step(amgsym_t h, const double* b_dev, do
     fail(AMGSYM_ERR_STATE, "setup did not build the value precision this mode needs (opts.precisions)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ensure_work(D, nrhs, vt);
+  if (preconditioner != AMGSYM_PC_AMG && preconditioner != AMGSYM_PC_AMGR)
+    fail(AMGSYM_ERR_ARG, "unknown preconditioner");
+  if (preconditioner == AMGSYM_PC_AMGR && !D->has_amgr)
+    fail(AMGSYM_ERR_STATE, "AMGR was not built (opts.amgr at setup)");
   Ctx c{D, nrhs * D->nb, vt, vmt, finest_hat != 0, st};
+  c.pc = preconditioner;
   c.fuse = true;
   prepare_cycle(c);
   cudaEvent_t held = nullptr;

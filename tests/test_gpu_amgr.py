@@ -98,3 +98,22 @@ def test_model_problem_amgr_beats_the_inner_block_amg():
         if s >= 1:
             assert ia.iters < im.iters, (s, rows[s])
     print("PCG iterations (AMGR, I (x) M_inn^-1) by s:", rows)
+
+
+def test_profile_step_with_amgr_times_its_launches():
+    """amgsym_profile_step with the AMGR preconditioner: the step's records
+    include AMGR's own launches (top smoother, restriction to the coarse
+    domain, the AMG of A_c) and leave the solve's result unchanged."""
+    N, s = (32, 32, 32), 3
+    P = amg.Problem.structured(N, 1.5, None, s).setup(amgr=1)
+    b = torch.from_numpy(rhs_uniform(P.n, 1, config=97)).to(DEV)
+    x1, i1 = P.solve(b, tol=1e-10, precision=amg.PREC_MIXED_FP32, preconditioner=amg.PC_AMGR)
+    recs = P.profile_step(b, torch.empty_like(b), 1, amg.PREC_MIXED_FP32, preconditioner=amg.PC_AMGR)
+    roles = [r["role"] for r in recs if r["phase"] == 1]
+    assert any("AMGR coarse-point smoother" in r for r in roles)
+    assert all(r["us"] > 0 for r in recs)
+    x2, i2 = P.solve(b, tol=1e-10, precision=amg.PREC_MIXED_FP32, preconditioner=amg.PC_AMGR)
+    assert i1.iters == i2.iters and torch.equal(x1, x2)
+    Q = amg.Problem.structured(N, 1.5, None, s).setup()
+    with pytest.raises(amg.AmgsymError):
+        Q.profile_step(b, torch.empty_like(b), 1, amg.PREC_MIXED_FP32, preconditioner=amg.PC_AMGR)
