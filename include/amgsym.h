@@ -142,6 +142,16 @@ typedef struct {
                                iterations on the 32^3 model problem against 9-11 for k = 1
                                (the paper pairs k = 2 with DPLS + energy minimisation) */
   int32_t amgr_interp_max;  /* AMGR interpolation weights kept per row, default 4 */
+  int32_t amgr_sym_ac;      /* 1 (default): the AMGR coarse problem's level-0 products with A_c
+                               run in the transformed basis: A_c = P^T A P keeps the dyadic
+                               structure (eq. "structAc"), so under the butterfly of eq. "P_s"
+                               it is blockdiag(A^_c,i), A^_c,i = P_b^T A_inn P_b + the
+                               interface couplings of block i; the product is the butterfly,
+                               the reduced SpMM over the 2^s interleaved columns (the inner
+                               block read once) with the coarse couplings, and the scaled
+                               butterfly back fused with the residual.  The same operator to
+                               rounding with about 1/2^s of the assembled A_c's matrix
+                               bytes.  0 = the assembled A_c (CSR) */
   int32_t zmarch;           /* 1: a finest-level diagonal-offset product whose
                                offsets are {0, +-1, +-gx, +-gxy} (a structured grid's 7-point
                                stencil: the reduced operator A^ and A_inn, or its FSAI factors

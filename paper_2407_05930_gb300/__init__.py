@@ -73,6 +73,7 @@ class Opts(ctypes.Structure):
         ("amgr", ctypes.c_int32),
         ("amgr_distance", ctypes.c_int32),
         ("amgr_interp_max", ctypes.c_int32),
+        ("amgr_sym_ac", ctypes.c_int32),
         ("zmarch", ctypes.c_int32),
         ("sell", ctypes.c_int32),
     ]

@@ -266,9 +266,11 @@ void launch_maxpy(const double* V, int64_t vstride, int32_t Cv, int32_t J, const
 void launch_colscale(const double* W, const double* s, double* out, int64_t rows, int32_t C, cudaStream_t st);
 // AMGR coarse step layouts (k_misc.cu): dir 0 from the transformed
 // [ncb][nrhs * nb] layout to the full coarse [ncb * nb][nrhs] layout (inverse
-// butterfly, scale 1/nb), dir 1 back (forward butterfly).  nb <= 16.
+// butterfly, scale 1/nb), dir 1 back (forward butterfly).  nb <= 16.  dir 0
+// writes alpha * (that) + beta * Z (Z in the output layout, read only when
+// beta != 0).
 void launch_coarse_relayout(VecType vt, const void* in, void* out, int64_t ncb, int32_t nrhs, int32_t nb, int dir,
-                            cudaStream_t st);
+                            cudaStream_t st, double alpha = 1.0, double beta = 0.0, const void* Z = nullptr);
 // A one-thread kernel that sleeps about naps x 10 us and returns (a bounded
 // loop, it waits on nothing): holds a stream while the host enqueues the
 // launches behind it, so that they then run back to back (per-launch timing).

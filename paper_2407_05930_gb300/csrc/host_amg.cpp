@@ -720,6 +720,7 @@ extern "C" amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts) {
   if ((o.precisions & 7) == 0) fail(AMGSYM_ERR_ARG, "precisions mask is empty");
   if (o.zmarch != 0 && o.zmarch != 1) fail(AMGSYM_ERR_ARG, "zmarch must be 0 or 1");
   if (o.sell != 0 && o.sell != 1) fail(AMGSYM_ERR_ARG, "sell must be 0 or 1");
+  if (o.amgr_sym_ac != 0 && o.amgr_sym_ac != 1) fail(AMGSYM_ERR_ARG, "amgr_sym_ac must be 0 or 1");
   if (o.amgr && (o.amgr_distance < 1 || o.amgr_distance > 4 || o.amgr_interp_max < 1))
     fail(AMGSYM_ERR_ARG, "amgr_distance must be in [1, 4] and amgr_interp_max >= 1");
   device_free(h);

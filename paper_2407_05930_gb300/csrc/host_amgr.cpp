@@ -217,6 +217,16 @@ void build_amgr(amgsym_problem* p, const amgsym_opts& o) {
       if (H->cf[i] > 0) cmap[i] = c++;
   }
   const int64_t ne = (int64_t)p->irow.size();
+  // the transformed-basis form: the fine couplings at coarse indices (cmap
+  // is increasing, so the entries stay sorted by (row, column))
+  H->cirow.resize(ne);
+  H->cicol.resize(ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    H->cirow[e] = cmap[p->irow[e]];
+    H->cicol[e] = cmap[p->icol[e]];
+    if (H->cirow[e] < 0 || H->cicol[e] < 0) fail(AMGSYM_ERR_STATE, "AMGR: an interface point is not coarse");
+  }
+  H->civals = p->ivals;
   // per coarse row: (coarse col, m, value) of the couplings to other copies
   std::vector<std::vector<std::tuple<int32_t, int32_t, double>>> cross(H->n_cb);
   for (int64_t e = 0; e < ne; ++e) {
@@ -246,6 +256,7 @@ void build_amgr(amgsym_problem* p, const amgsym_opts& o) {
       Ac.ptr[lc * nb + j + 1] = (int64_t)Ac.idx.size();
     }
   sort_rows(Ac);
+  H->Ac0 = std::move(Ac0);
   // merge duplicate columns (none expected: H_m of distinct m land in distinct copies)
   // the coarse problem: s = 0, its own standard AMG hierarchy
   auto* cp = new amgsym_problem();

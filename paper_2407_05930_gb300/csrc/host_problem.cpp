@@ -66,6 +66,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->amgr = 0;
   o->amgr_distance = 1;
   o->amgr_interp_max = 4;
+  o->amgr_sym_ac = 1;
   o->zmarch = 0;
   o->sell = 0;
 }

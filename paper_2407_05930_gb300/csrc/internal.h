@@ -79,6 +79,12 @@ struct HostAmgr {
   double omegaK = 1.0;      // damping of the fine-point smoother
   std::vector<double> jdC;  // coarse rows: omega_C / a_ll (the FSAI of C-bar with a diagonal pattern); fine rows 0
   Csr Ac;                   // full reduced operator, n_cb * 2^s rows, copy index fastest
+  // A_c in the transformed basis (eq. "structAc" under P_s): block i is
+  // Ac0 + the interface couplings of block i, Ac0 = P_b^T A_inn P_b; the
+  // couplings are the fine ones (ivals, [entry][block]) at coarse indices
+  Csr Ac0;
+  std::vector<int32_t> cirow, cicol;
+  std::vector<double> civals;
   std::shared_ptr<amgsym_problem> coarse;  // Ac with its AMG hierarchy (and device copies)
 };
 

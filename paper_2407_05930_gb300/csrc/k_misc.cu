@@ -551,40 +551,70 @@ void launch_sub_block0_mean(double* X, int64_t rows, int32_t nrhs, int32_t nb, d
 // 2^s], column r * 2^s + i = block i) and the full coarse domain of the
 // coarse problem ([n_cb * 2^s][nrhs], row l * 2^s + j = copy j), by the
 // Walsh-Hadamard butterfly of eq. "P_s": out_j = scale * sum_i s(i, j) in_i
-// with s(i, j) = (-1)^popcount(i & j) (dir 0: scale 2^-s; dir 1: scale 1).
-template <typename T>
+// with s(i, j) = (-1)^popcount(i & j) (dir 0: scale 2^-s; dir 1: scale 1),
+// as the fast transform (log2(nb) stages of sums and differences) in the
+// vector precision.  dir 0 may also take an epilogue: out = alpha * (the
+// butterfly) + beta * Z (Z in the output layout; beta = 0 reads no Z),
+// e.g. the residual y - A_c z.
+template <typename T, int NB>
 __global__ void __launch_bounds__(kBlock) coarse_relayout_kernel(const T* __restrict__ in, T* __restrict__ out,
-                                                                 int64_t ncb, int32_t nrhs, int32_t nb, int dir) {
+                                                                 int64_t ncb, int32_t nrhs, int dir, double alpha,
+                                                                 double beta, const T* __restrict__ Z) {
   const int64_t total = ncb * nrhs;
-  const double scale = dir == 0 ? 1.0 / nb : 1.0;
+  const T scale = dir == 0 ? (T)(alpha / NB) : (T)1;
+  const T tb = (T)beta;
   for (int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x; t < total; t += (int64_t)gridDim.x * kBlock) {
     const int64_t l = t / nrhs;
     const int32_t r = (int32_t)(t - l * nrhs);
-    double v[16];
-    for (int32_t i = 0; i < nb; ++i)
-      v[i] = dir == 0 ? (double)in[l * nrhs * nb + (int64_t)r * nb + i] : (double)in[(l * nb + i) * nrhs + r];
-    for (int32_t j = 0; j < nb; ++j) {
-      double acc = 0.0;
-      for (int32_t i = 0; i < nb; ++i) acc += (__popc((unsigned)(i & j)) & 1) ? -v[i] : v[i];
-      const T o = (T)(scale * acc);
-      if (dir == 0)
-        out[(l * nb + j) * nrhs + r] = o;
-      else
-        out[l * nrhs * nb + (int64_t)r * nb + j] = o;
+    T v[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      v[i] = dir == 0 ? in[l * nrhs * NB + (int64_t)r * NB + i] : in[(l * NB + i) * nrhs + r];
+#pragma unroll
+    for (int h = 1; h < NB; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+        if (!(i & h)) {
+          const T a = v[i], b = v[i + h];
+          v[i] = a + b;
+          v[i + h] = a - b;
+        }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (dir == 0) {
+        const int64_t o = (l * NB + j) * nrhs + r;
+        out[o] = beta != 0.0 ? scale * v[j] + tb * Z[o] : scale * v[j];
+      } else {
+        out[l * nrhs * NB + (int64_t)r * NB + j] = v[j];
+      }
     }
   }
 }
 
+template <typename T>
+static void relayout_t(const void* in, void* out, int64_t ncb, int32_t nrhs, int32_t nb, int dir, double alpha,
+                       double beta, const void* Z, int g, cudaStream_t st) {
+  const T* i = static_cast<const T*>(in);
+  T* o = static_cast<T*>(out);
+  const T* z = static_cast<const T*>(Z);
+  switch (nb) {
+    case 1: coarse_relayout_kernel<T, 1><<<g, kBlock, 0, st>>>(i, o, ncb, nrhs, dir, alpha, beta, z); break;
+    case 2: coarse_relayout_kernel<T, 2><<<g, kBlock, 0, st>>>(i, o, ncb, nrhs, dir, alpha, beta, z); break;
+    case 4: coarse_relayout_kernel<T, 4><<<g, kBlock, 0, st>>>(i, o, ncb, nrhs, dir, alpha, beta, z); break;
+    case 8: coarse_relayout_kernel<T, 8><<<g, kBlock, 0, st>>>(i, o, ncb, nrhs, dir, alpha, beta, z); break;
+    case 16: coarse_relayout_kernel<T, 16><<<g, kBlock, 0, st>>>(i, o, ncb, nrhs, dir, alpha, beta, z); break;
+    default: fail(AMGSYM_ERR_ARG, "coarse relayout: 2^s must be at most 16");
+  }
+}
+
 void launch_coarse_relayout(VecType vt, const void* in, void* out, int64_t ncb, int32_t nrhs, int32_t nb, int dir,
-                            cudaStream_t st) {
+                            cudaStream_t st, double alpha, double beta, const void* Z) {
   count_launch();
   const int g = grid_for(ncb * nrhs, kBlock);
   if (vt == VEC_F64)
-    coarse_relayout_kernel<double><<<g, kBlock, 0, st>>>(static_cast<const double*>(in), static_cast<double*>(out),
-                                                         ncb, nrhs, nb, dir);
+    relayout_t<double>(in, out, ncb, nrhs, nb, dir, alpha, beta, Z, g, st);
   else
-    coarse_relayout_kernel<float><<<g, kBlock, 0, st>>>(static_cast<const float*>(in), static_cast<float*>(out), ncb,
-                                                        nrhs, nb, dir);
+    relayout_t<float>(in, out, ncb, nrhs, nb, dir, alpha, beta, Z, g, st);
 }
 
 __global__ void hold_kernel(int32_t naps) {

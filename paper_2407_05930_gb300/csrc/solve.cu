@@ -226,6 +226,43 @@ static bool build_halo(const Csr& M, int64_t budget_bytes, HostHalo& H) {
   return false;
 }
 
+// Interface couplings (entries sorted by (row, column), values [entry][block])
+// in the per-row flag form the SpMM looks up (see DevIface).
+static DevIface upload_iface(std::vector<void*>& owner, int64_t rows, const std::vector<int32_t>& irow,
+                             const std::vector<int32_t>& icol, const std::vector<double>& ivals, int32_t nb) {
+  DevIface F;
+  const int64_t ne = (int64_t)irow.size();
+  if (ne <= 0) return F;
+  const int64_t words = (rows + 31) / 32;
+  std::vector<uint32_t> mask(words, 0);
+  std::vector<int32_t> prefix(words, 0), iptr, irows;
+  for (int64_t e = 0; e < ne; ++e) {
+    const int32_t r = irow[e];
+    if (e == 0 || irow[e - 1] != r) {
+      mask[r >> 5] |= 1u << (r & 31);
+      iptr.push_back((int32_t)e);
+      irows.push_back(r);
+    }
+  }
+  iptr.push_back((int32_t)ne);
+  int32_t run = 0;
+  for (int64_t w = 0; w < words; ++w) {
+    prefix[w] = run;
+    run += __builtin_popcount(mask[w]);
+  }
+  F.n_rows_flagged = run;
+  F.n_entries = ne;
+  F.mask = upload(owner, mask.data(), words);
+  F.prefix = upload(owner, prefix.data(), words);
+  F.iptr = upload(owner, iptr.data(), (int64_t)iptr.size());
+  F.irows = upload(owner, irows.data(), (int64_t)irows.size());
+  F.icol = upload(owner, icol.data(), ne);
+  F.ival64 = upload(owner, ivals.data(), ne * nb);
+  std::vector<float> v32(ivals.begin(), ivals.end());
+  F.ival32 = upload(owner, v32.data(), ne * nb);
+  return F;
+}
+
 // Sliced form (SELL-32) of a CSR matrix, see DevCsr: rows sorted by length
 // (longest first, stable) within windows of kSellWindow rows, then cut into
 // slices of 32; false when the padded entries would not fit 32-bit offsets.
@@ -438,36 +475,7 @@ void device_upload(amgsym_problem* p) {
   }
   D->Ainn = D->lv[0].A;
   // interface couplings
-  const int64_t ne = (int64_t)p->irow.size();
-  if (ne > 0) {
-    const int64_t words = (p->n_b + 31) / 32;
-    std::vector<uint32_t> mask(words, 0);
-    std::vector<int32_t> prefix(words, 0), iptr, irows;
-    for (int64_t e = 0; e < ne; ++e) {
-      const int32_t r = p->irow[e];
-      if (e == 0 || p->irow[e - 1] != r) {
-        mask[r >> 5] |= 1u << (r & 31);
-        iptr.push_back((int32_t)e);
-        irows.push_back(r);
-      }
-    }
-    iptr.push_back((int32_t)ne);
-    int32_t run = 0;
-    for (int64_t w = 0; w < words; ++w) {
-      prefix[w] = run;
-      run += __builtin_popcount(mask[w]);
-    }
-    D->iface.n_rows_flagged = run;
-    D->iface.n_entries = ne;
-    D->iface.mask = upload(D->owned, mask.data(), words);
-    D->iface.prefix = upload(D->owned, prefix.data(), words);
-    D->iface.iptr = upload(D->owned, iptr.data(), (int64_t)iptr.size());
-    D->iface.irows = upload(D->owned, irows.data(), (int64_t)irows.size());
-    D->iface.icol = upload(D->owned, p->icol.data(), ne);
-    D->iface.ival64 = upload(D->owned, p->ivals.data(), ne * p->nb);
-    std::vector<float> v32(p->ivals.begin(), p->ivals.end());
-    D->iface.ival32 = upload(D->owned, v32.data(), ne * p->nb);
-  }
+  D->iface = upload_iface(D->owned, p->n_b, p->irow, p->icol, p->ivals, p->nb);
   // AMGR top level and its coarse problem
   if (p->amgr) {
     const HostAmgr& M = *p->amgr;
@@ -487,6 +495,15 @@ void device_upload(amgsym_problem* p) {
     device_upload(cp);
     CK(cudaSetDevice(D->device_id));
     G.cd = cp->dev;
+    if (p->opts.amgr_sym_ac && p->nb > 1) {
+      // the coarse problem's level-0 products in the transformed basis
+      auto S = std::make_shared<SymCoarse>();
+      S->inn = upload_csr(G.cd->owned, M.Ac0, D->precisions);
+      S->iface = upload_iface(G.cd->owned, M.n_cb, M.cirow, M.cicol, M.civals, p->nb);
+      S->nb = p->nb;
+      S->n_cb = M.n_cb;
+      G.cd->symc = S;
+    }
     D->has_amgr = true;
   }
   // persistent coarse cycle from the first level below the finest with at
@@ -568,6 +585,10 @@ void ensure_work(Device* D, int32_t nrhs, VecType vt) {
   W.z = vec(D->n_b);
   W.p = vec(D->n_b);
   W.q = vec(D->n_b);
+  if (D->symc) {  // [n_cb][nrhs * 2^s]: the same size as the copy layout
+    W.sxh = vec(D->n_b);
+    W.syh = vec(D->n_b);
+  }
   if (D->has_amgr) {
     W.at = vec(D->n_b);
     W.ar = vec(D->n_b);
@@ -813,6 +834,51 @@ static void run_jacobi(const Ctx& c, const DevLevel& L, const void* jd, const vo
            level_of(c, L), xsize(c.vt) * (int64_t)L.n * (1 + (int64_t)c.C * (accumulate ? 3 : 2)));
 }
 
+// r = y - A_l z.  On level 0 of the AMGR coarse problem with its
+// transformed-basis operator (SymCoarse): butterfly z to the transformed
+// layout, the reduced SpMM with the coarse couplings, and the scaled
+// butterfly back with the residual epilogue.
+static void level_residual(const Ctx& c, const DevLevel& L, const void* z, void* r, const void* y, bool hat) {
+  Device* D = c.D;
+  if (D->symc && &L == &D->lv[0]) {
+    const SymCoarse& S = *D->symc;
+    PrecWork& W = c.vt == VEC_F64 ? D->w64 : D->w32;
+    const int32_t nrhs = c.C;  // the coarse problem has one column per right-hand side
+    {
+      ProfScope ps(c.st);
+      launch_coarse_relayout(c.vt, z, W.sxh, S.n_cb, nrhs, S.nb, 1, c.st);
+      check_launch();
+      if (ps.on())
+        ps.end(std::string("coarse_relayout_kernel<") + tname(c.vt) + ">", "AMGR A_c: to the transformed basis", 0,
+               2 * xsize(c.vt) * S.n_cb * S.nb * nrhs);
+    }
+    Ctx ch = c;
+    ch.C = nrhs * S.nb;
+    SpmmArgs a = make_spmm_args(ch, S.inn, c.mt, c.vt, c.vt, W.sxh, W.syh, 1.0, 0.0, nullptr, false, nullptr);
+    if (S.iface.mask) {
+      a.imask = S.iface.mask;
+      a.iprefix = S.iface.prefix;
+      a.iptr = S.iface.iptr;
+      a.irows = S.iface.irows;
+      a.nflag = S.iface.n_rows_flagged;
+      a.icol = S.iface.icol;
+      a.ival = (c.mt == VAL_F64 || c.vt == VEC_F64) ? (const void*)S.iface.ival64 : (const void*)S.iface.ival32;
+      a.nb = S.nb;
+    }
+    run_spmm(ch, S.inn, c.mt, c.vt, c.vt, a);
+    {
+      ProfScope ps(c.st);
+      launch_coarse_relayout(c.vt, W.syh, r, S.n_cb, nrhs, S.nb, 0, c.st, -1.0, 1.0, y);
+      check_launch();
+      if (ps.on())
+        ps.end(std::string("coarse_relayout_kernel<") + tname(c.vt) + ">", "AMGR A_c: back, r = y - A_c z", 0,
+               3 * xsize(c.vt) * S.n_cb * S.nb * nrhs);
+    }
+    return;
+  }
+  spmm(c, L.A, c.mt, c.vt, c.vt, z, r, -1.0, 1.0, y, hat, nullptr);
+}
+
 static void smooth_first(const Ctx& c, const DevLevel& L, LevelWork& lw, const void* y, void* z) {
   if (const void* jd = L.jd(c.vt)) {
     run_jacobi(c, L, jd, y, z, 0);
@@ -824,7 +890,7 @@ static void smooth_first(const Ctx& c, const DevLevel& L, LevelWork& lw, const v
 
 static void smooth_sweep(const Ctx& c, const DevLevel& L, LevelWork& lw, const void* y, void* z, bool hat,
                          const DotArgs* dot) {
-  spmm(c, L.A, c.mt, c.vt, c.vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+  level_residual(c, L, z, lw.r, y, hat);
   const void* jd = L.jd(c.vt);
   if (jd && !dot) {
     run_jacobi(c, L, jd, lw.r, z, 1);
@@ -1014,7 +1080,7 @@ static const void* vcycle_level(const Ctx& c, std::vector<LevelWork>& lws, int l
   if (!pre_done) smooth_first(c, L, lw, y, z);
   for (int k = 1; k < D->nu; ++k) smooth_sweep(c, L, lw, y, z, hat, nullptr);
   // residual and restriction r_c = P^T (y - A z)
-  spmm(c, L.A, mt, vt, vt, z, lw.r, -1.0, 1.0, y, hat, nullptr);
+  level_residual(c, L, z, lw.r, y, hat);
   LevelWork& cw = lws[l + 1];
   const DevLevel& Lc = D->lv[l + 1];
   const bool persist_next = c.fuse && l + 1 == D->fuse_level;

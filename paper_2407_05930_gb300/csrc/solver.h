@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <memory>
 #include <set>
 #include <string>
 #include <tuple>
@@ -42,6 +43,9 @@ struct PrecWork {
   // residual and coarse correction [n_cb][C], the same in the coarse
   // problem's layout [n_cb * 2^s][nrhs]
   void *at = nullptr, *ar = nullptr, *arc = nullptr, *ahc = nullptr, *arc2 = nullptr, *ahc2 = nullptr;
+  // AMGR coarse problem with the transformed-basis A_c (SymCoarse): the
+  // operand and product in that layout [n_cb][nrhs * 2^s]
+  void *sxh = nullptr, *syh = nullptr;
 };
 
 struct GraphKey {
@@ -96,8 +100,24 @@ struct DevAmgr {
   const void* jd(VecType t) const { return t == VEC_F64 ? (const void*)jd64 : (const void*)jd32; }
 };
 
+// The AMGR coarse operator in the transformed basis: A_c = (1 / 2^s) H
+// blockdiag(A^_c,i) H with A^_c,i = Ac0 + interface couplings of block i, so
+// a product with A_c (the copy layout of the coarse problem) is the butterfly
+// to the transformed layout, the reduced SpMM (Ac0 read once for every block
+// and right-hand side, the couplings in the interface pass), and the scaled
+// butterfly back: about 1/2^s of the matrix bytes of the assembled A_c.
+struct SymCoarse {
+  DevCsr inn;      // Ac0 = P_b^T A_inn P_b, n_cb rows
+  DevIface iface;  // coarse interface couplings, per block
+  int32_t nb = 1;
+  int64_t n_cb = 0;
+};
+
 struct Device {
   int device_id = 0;
+  // set on the AMGR coarse problem's device: its level-0 A products run in
+  // the transformed basis (opts.amgr_sym_ac of the fine problem)
+  std::shared_ptr<SymCoarse> symc;
   uint64_t epoch = 0;      // next_generation() at upload: identifies this Device
   uint64_t work_gen = 0;   // next_generation() whenever work arrays are (re)allocated
   uint64_t tiles_gen = 0;  // bumped whenever the tuner changes tiles

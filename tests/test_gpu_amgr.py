@@ -117,3 +117,34 @@ def test_profile_step_with_amgr_times_its_launches():
     Q = amg.Problem.structured(N, 1.5, None, s).setup()
     with pytest.raises(amg.AmgsymError):
         Q.profile_step(b, torch.empty_like(b), 1, amg.PREC_MIXED_FP32, preconditioner=amg.PC_AMGR)
+
+
+@pytest.mark.parametrize("prec", [amg.PREC_FP64, amg.PREC_MIXED_FP32])
+def test_transformed_basis_coarse_operator_equals_the_assembled_one(prec):
+    """opts.amgr_sym_ac: the coarse problem's level-0 products with A_c run as
+    butterfly -> reduced SpMM (P_b^T A_inn P_b read once, coarse couplings)
+    -> scaled butterfly (eq. "structAc" under eq. "P_s").  The same operator
+    to rounding: AMGR applications agree with those of the assembled A_c, and
+    the solves converge alike."""
+    N, s = (24, 20, 16), 3
+    g = gaussian_logk(N, s, seed=98, corr=2.0)
+    P1 = amg.Problem.structured(N, 1.5, g, s).setup(amgr=1, amgr_sym_ac=1, coarse_max=64)
+    P0 = amg.Problem.structured(N, 1.5, g, s).setup(amgr=1, amgr_sym_ac=0, coarse_max=64)
+    dt = torch.float64 if prec == amg.PREC_FP64 else torch.float32
+    U = torch.from_numpy(np.random.default_rng(9).standard_normal((P1.n_b, 2 << s))).to(DEV, dt)
+    Z1, Z0 = torch.empty_like(U), torch.empty_like(U)
+    P1.amgr_apply(U, Z1, 2, prec)
+    P0.amgr_apply(U, Z0, 2, prec)
+    d = (Z1 - Z0).double().norm() / Z0.double().norm()
+    assert d <= (1e-12 if prec == amg.PREC_FP64 else 1e-5), float(d)
+    b = torch.from_numpy(rhs_uniform(P1.n, 1, config=99)).to(DEV)
+    x1, i1 = P1.solve(b, tol=1e-10, precision=prec, preconditioner=amg.PC_AMGR)
+    x0, i0 = P0.solve(b, tol=1e-10, precision=prec, preconditioner=amg.PC_AMGR)
+    assert i1.converged and i0.converged and abs(i1.iters - i0.iters) <= 1
+    assert (x1 - x0).norm() <= 1e-8 * x0.norm()
+    roles = [r["role"] for r in P1.profile_step(b, torch.empty_like(b), 1, amg.PREC_MIXED_FP32,
+                                                 preconditioner=amg.PC_AMGR)]
+    assert any("AMGR A_c: to the transformed basis" in r for r in roles)
+    roles0 = [r["role"] for r in P0.profile_step(b, torch.empty_like(b), 1, amg.PREC_MIXED_FP32,
+                                                  preconditioner=amg.PC_AMGR)]
+    assert not any("AMGR A_c" in r for r in roles0)
