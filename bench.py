@@ -551,7 +551,8 @@ def run_gpu(args):
     t_setup = time.time()
     g = gaussian_logk(N, s, seed=FIELD_SEED, corr=8.0)
     # amgr=1 also builds AMGR (Sec. 3.2) beside the I (x) M_inn hierarchy, for its variant line
-    P = amg.Problem.structured(N, 1.5, g, s).setup(precisions=3, amgr=0 if args.profile_only else 1)
+    with_amgr = not args.profile_only or args.profile_only.startswith("amgr")
+    P = amg.Problem.structured(N, 1.5, g, s).setup(precisions=3, amgr=1 if with_amgr else 0)
     b_host = rhs_uniform(P.n, nrhs, config=3)
     b = torch.from_numpy(b_host).to(dev)
     x = torch.empty_like(b)
@@ -567,11 +568,14 @@ def run_gpu(args):
     if args.profile_only:
         # one warm-up solve, then the marked work only (for ncu launch lists)
         kw = fp64 if args.profile_only == "fp64" else mixed
+        if args.profile_only.startswith("amgr"):
+            kw = dict(mixed, preconditioner=amg.PC_AMGR)
         P.solve(b, x, **kw)
         torch.cuda.synchronize()
-        if args.profile_only == "step":
+        if args.profile_only in ("step", "amgr_step"):
+            pc = amg.PC_AMGR if args.profile_only == "amgr_step" else amg.PC_AMG
             torch.cuda.nvtx.range_push("profile_step")
-            recs = P.profile_step(b, x, nrhs, amg.PREC_MIXED_FP32)
+            recs = P.profile_step(b, x, nrhs, amg.PREC_MIXED_FP32, preconditioner=pc)
             torch.cuda.nvtx.range_pop()
             for r in recs:
                 print(json.dumps(r))
@@ -825,7 +829,7 @@ def main():
     ap.add_argument("--profile-grid", type=int, default=256, help="--profile-only: cells per axis")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--no-tune", action="store_true", help="batched: fixed tiles instead of the autotuner")
-    ap.add_argument("--profile-only", choices=["mixed", "fp64", "step"], default=None,
+    ap.add_argument("--profile-only", choices=["mixed", "fp64", "step", "amgr", "amgr_step"], default=None,
                     help="run one marked solve (or one profiled step) and nothing else (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":

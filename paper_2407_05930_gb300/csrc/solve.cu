@@ -144,7 +144,10 @@ static void run_spmm(const Ctx& c, const DevCsr& M, ValType mt, VecType xt, VecT
                              (ifc ? "1" : "0") + "," + (dia ? "1" : "0") + ">";
   int level = -1;
   std::string role;
-  if (ifc) {
+  if (ifc && c.D->symc && M.idx == c.D->symc->inn.idx) {
+    role = "AMGR A_c in the transformed basis";
+    level = 0;
+  } else if (ifc) {
     role = xt == VEC_F64 && ot == VEC_F32 ? "FP64 outer residual b^ - A^ x^" : "reduced SpMM A^ p";
     level = -1;
   } else {
