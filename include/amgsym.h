@@ -186,6 +186,13 @@ typedef struct {
                                (a 256-row warp-pair covers scattered rows; the CSR kernel's 8
                                neighbouring rows per warp share their gathers), 90 ms a mixed
                                solve against 67; the FP64 solve ran 254 ms against 282 */
+  int32_t lambda_device;    /* 1 (default): the smoother damping's lambda_max(G A G^T) of every
+                               level is estimated on the device after the upload (the host
+                               estimator's steps: 30 power iterations with Rayleigh quotients
+                               from the same seeded start vector, FP64 products), not by the
+                               host setup; host_only setups always use the host estimator.
+                               0 = host.  (Where a coarse level has no FP64 values, opts.
+                               precisions without 1, its estimate stays on the host.) */
 } amgsym_opts;
 
 #define AMGSYM_MAX_DIAG 8

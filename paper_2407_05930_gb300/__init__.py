@@ -76,6 +76,7 @@ class Opts(ctypes.Structure):
         ("amgr_sym_ac", ctypes.c_int32),
         ("zmarch", ctypes.c_int32),
         ("sell", ctypes.c_int32),
+        ("lambda_device", ctypes.c_int32),
     ]
 
 

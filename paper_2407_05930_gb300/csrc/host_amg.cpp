@@ -606,8 +606,14 @@ void build_hierarchy(const Csr& A0, const amgsym_opts& o, HostHierarchy& H) {
     }
     L.G = fsai(L.A, lev == 0 ? o.fsai_max_lower : o.fsai_max_lower_coarse);
     L.Gt = transpose(L.G);
-    L.lambda_max = lambda_max_GAGt(L.A, L.G, L.Gt, o.seed + 17 * (uint64_t)lev);
-    L.omega = (L.lambda_max > 0.0) ? o.omega_scale / L.lambda_max : 1.0;
+    if (o.lambda_device && !o.host_only) {
+      // estimated on the device after the upload (device_upload), same steps
+      L.lambda_max = 0.0;
+      L.omega = 0.0;
+    } else {
+      L.lambda_max = lambda_max_GAGt(L.A, L.G, L.Gt, o.seed + 17 * (uint64_t)lev);
+      L.omega = (L.lambda_max > 0.0) ? o.omega_scale / L.lambda_max : 1.0;
+    }
     L.P = std::move(P);
     L.R = transpose(L.P);
     Csr AP = spgemm(L.A, L.P);
@@ -721,6 +727,7 @@ extern "C" amgsym_status amgsym_setup(amgsym_t h, const amgsym_opts* opts) {
   if (o.zmarch != 0 && o.zmarch != 1) fail(AMGSYM_ERR_ARG, "zmarch must be 0 or 1");
   if (o.sell != 0 && o.sell != 1) fail(AMGSYM_ERR_ARG, "sell must be 0 or 1");
   if (o.amgr_sym_ac != 0 && o.amgr_sym_ac != 1) fail(AMGSYM_ERR_ARG, "amgr_sym_ac must be 0 or 1");
+  if (o.lambda_device != 0 && o.lambda_device != 1) fail(AMGSYM_ERR_ARG, "lambda_device must be 0 or 1");
   if (o.amgr && (o.amgr_distance < 1 || o.amgr_distance > 4 || o.amgr_interp_max < 1))
     fail(AMGSYM_ERR_ARG, "amgr_distance must be in [1, 4] and amgr_interp_max >= 1");
   device_free(h);

@@ -69,6 +69,7 @@ extern "C" void amgsym_opts_default(amgsym_opts* o) {
   o->amgr_sym_ac = 1;
   o->zmarch = 0;
   o->sell = 0;
+  o->lambda_device = 1;
 }
 
 extern "C" void amgsym_solve_opts_default(amgsym_solve_opts* o) {

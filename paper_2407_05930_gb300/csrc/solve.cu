@@ -11,6 +11,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <random>
 #include <map>
 #include <mutex>
 #include <set>
@@ -429,6 +430,52 @@ void device_free(amgsym_problem* p) {
   p->dev = nullptr;
 }
 
+// lambda_max(G A G^T) on the device: the steps of the host estimator
+// (lambda_max_GAGt: uniform[-1, 1] start from the same seed, 30 power
+// iterations, each normalised, the Rayleigh quotient of the last) with FP64
+// products on the uploaded matrices.
+static double device_lambda_max(Device* D, const DevCsr& A, const DevCsr& G, const DevCsr& Gt, int64_t n,
+                                uint64_t seed) {
+  std::vector<double> h((size_t)n);
+  std::mt19937_64 rng(seed ^ 0x9e3779b97f4a7c15ULL);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  for (auto& x : h) x = U(rng);
+  std::vector<void*> tmp;
+  double* v = dalloc<double>(tmp, n);
+  double* t1 = dalloc<double>(tmp, n);
+  double* t2 = dalloc<double>(tmp, n);
+  double* t3 = dalloc<double>(tmp, n);
+  double* part = dalloc<double>(tmp, (int64_t)mdot_blocks(n, 1));
+  double* s = dalloc<double>(tmp, 1);
+  struct Free {
+    std::vector<void*>& t;
+    ~Free() {
+      for (void* q : t) cudaFree(q);
+    }
+  } fr{tmp};
+  CK(cudaMemcpy(v, h.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+  Ctx c{D, 1, VEC_F64, VAL_F64, false, nullptr};
+  double lam = 0.0, nv2 = 0.0, num = 0.0;
+  for (int it = 0; it < 30; ++it) {
+    launch_mdot(v, 0, 1, 1, v, n, 1, part, s, nullptr);
+    check_launch();
+    CK(cudaMemcpy(&nv2, s, sizeof(double), cudaMemcpyDeviceToHost));
+    if (!(nv2 > 0.0)) break;
+    const double inv = 1.0 / std::sqrt(nv2);
+    CK(cudaMemcpy(s, &inv, sizeof(double), cudaMemcpyHostToDevice));
+    launch_colscale(v, s, v, n, 1, nullptr);
+    spmm(c, Gt, VAL_F64, VEC_F64, VEC_F64, v, t1, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, A, VAL_F64, VEC_F64, VEC_F64, t1, t2, 1.0, 0.0, nullptr, false, nullptr);
+    spmm(c, G, VAL_F64, VEC_F64, VEC_F64, t2, t3, 1.0, 0.0, nullptr, false, nullptr);
+    launch_mdot(v, 0, 1, 1, t3, n, 1, part, s, nullptr);
+    check_launch();
+    CK(cudaMemcpy(&num, s, sizeof(double), cudaMemcpyDeviceToHost));
+    lam = num;
+    std::swap(v, t3);
+  }
+  return lam;
+}
+
 void device_upload(amgsym_problem* p) {
   device_free(p);
   auto* D = new Device();
@@ -444,10 +491,10 @@ void device_upload(amgsym_problem* p) {
   D->n_b = p->n_b;
   if (p->s > 4) fail(AMGSYM_ERR_ARG, "device path supports s <= 4");
   D->perm = upload(D->owned, p->perm.data(), (int64_t)p->perm.size());
-  const auto& H = p->H;
+  auto& H = p->H;
   D->lv.resize(H.levels.size());
   for (size_t l = 0; l < H.levels.size(); ++l) {
-    const HostLevel& L = H.levels[l];
+    HostLevel& L = H.levels[l];
     DevLevel& V = D->lv[l];
     V.n = (int32_t)L.A.rows;
     V.omega = L.omega;
@@ -462,6 +509,16 @@ void device_upload(amgsym_problem* p) {
       V.R = upload_csr(D->owned, L.R, p->opts.precisions, nullptr, hkb, sl);
       V.G = upload_csr(D->owned, L.G, p->opts.precisions, &L.Gdia, hkb, sl);
       V.Gt = upload_csr(D->owned, L.Gt, p->opts.precisions, &L.Gtdia, hkb, sl);
+      if (p->opts.lambda_device && !(L.omega > 0.0)) {
+        // the damping's lambda_max, deferred by the host setup
+        const uint64_t seed = p->opts.seed + 17 * (uint64_t)l;
+        if (V.A.v64 && V.G.v64 && V.Gt.v64)
+          L.lambda_max = device_lambda_max(D, V.A, V.G, V.Gt, L.A.rows, seed);
+        else
+          L.lambda_max = lambda_max_GAGt(L.A, L.G, L.Gt, seed);
+        L.omega = (L.lambda_max > 0.0) ? p->opts.omega_scale / L.lambda_max : 1.0;
+        V.omega = L.omega;
+      }
       // a diagonal FSAI factor: the smoother is the diagonal omega g_ii^2
       bool diag = L.G.nnz() == L.G.rows;
       for (int64_t i = 0; diag && i < L.G.rows; ++i) diag = L.G.idx[L.G.ptr[i]] == (int32_t)i;

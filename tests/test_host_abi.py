@@ -277,14 +277,14 @@ def test_update_values_replaces_blocks_and_rejects_broken_symmetry(N, s):
     assert P.num_levels() >= 2
 
 
-@pytest.mark.parametrize("name", ["zmarch", "sell", "amgr_sym_ac"])
+@pytest.mark.parametrize("name", ["zmarch", "sell", "amgr_sym_ac", "lambda_device"])
 def test_kernel_form_options_are_validated(name):
     """The kernel-form switches (z-marching stencil, sliced CSR, AMGR coarse
     operator in the transformed basis) take 0 or 1; their defaults are
     reported by amgsym_opts_default."""
     o = amg.default_opts()
     assert getattr(o, name) in (0, 1)
-    assert (o.zmarch, o.sell, o.amgr_sym_ac) == (0, 0, 1)
+    assert (o.zmarch, o.sell, o.amgr_sym_ac, o.lambda_device) == (0, 0, 1, 1)
     P = amg.Problem.structured((8, 8, 8), 0.0, None, 1)
     with pytest.raises(amg.AmgsymError) as e:
         P.setup(host_only=1, **{name: 2})
