@@ -822,14 +822,17 @@ void tune_tiles(const Ctx& c) {
     jobs.push_back({&L.A, c.mt, W.lw[l].t, W.lw[l].r, false});
     jobs.push_back({&L.G, c.mt, W.lw[l].t, W.lw[l].r, false});
     jobs.push_back({&L.Gt, c.mt, W.lw[l].t, W.lw[l].r, false});
-    // the last finest-level smoother update z += w G^T (...) with <r, z>
-    if (l == 0) jobs.push_back({&L.Gt, c.mt, W.lw[l].t, W.lw[l].r, false, true, 1.0, W.lw[l].z});
+    // the last finest-level smoother update z += w G^T (...) with <r, z>: the
+    // partner is the PCG's r, as in the solve (level 0 has no level z vector)
+    if (l == 0) jobs.push_back({&L.Gt, c.mt, W.lw[l].t, W.lw[l].r, false, true, 1.0, W.r});
     jobs.push_back({&L.R, c.mt, W.lw[l].r, W.lw[l + 1].y, false});
     jobs.push_back({&L.P, c.mt, W.lw[l + 1].z, W.lw[l].t, false});
   }
   const int vmax = c.vt == VEC_F64 ? 2 : 4;
   for (const Job& j : jobs) {
     if (!j.M->vals(j.mt)) continue;
+    if (!j.X || !j.Y || (j.dot && !j.W))
+      fail(AMGSYM_ERR_STATE, "tile tuner: a work vector of a timed product is missing");
     Tile best;
     float best_ms = 1e30f;
     for (int cm = 1; cm <= 2; ++cm) {
