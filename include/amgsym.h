@@ -358,8 +358,9 @@ amgsym_status amgsym_solve(amgsym_t h, const double* b_dev, double* x_dev, int32
  * Eigenpair search (both setups): thick-restarted Lanczos with full
  * reorthogonalisation (Wu and Simon) on a basis of `steps` vectors,
  * restarted from the max(k + 4, steps / 2) (at most steps - 2) smallest Ritz
- * vectors, until the k smallest Ritz pairs have residual norms <= tol *
- * lambda (at most 200 restarts); then up to 3 more such runs from new
+ * vectors, until the k smallest Ritz pairs and max(4, k / 2) more (as the
+ * basis allows) have residual norms <= tol * lambda (at most 200 restarts);
+ * then up to 3 more such runs from new
  * random vectors kept orthogonal to every pair found (so every copy of a
  * multiple eigenvalue is found), stopping when a run finds nothing below the
  * k-th smallest value so far.  Start vectors are uniform[-1, 1] from `seed`.

@@ -470,11 +470,11 @@ class Problem:
 
     @staticmethod
     def _ritz_steps(k: int, steps: Optional[int]) -> int:
-        return int(steps) if steps is not None else max(40, 2 * int(k) + 8)
+        return int(steps) if steps is not None else max(40, 3 * int(k) + 8)
 
     def lrc_setup(self, k: int, steps: Optional[int] = None, tol: float = 0.1, seed: int = 7):
         """LRCAMG(k): the k smallest eigenpairs of M_inn^{-1} A^_i per block (amgsym_lrc_setup);
-        steps = the restarted Lanczos basis size (default max(40, 2k + 8))."""
+        steps = the restarted Lanczos basis size (default max(40, 3k + 8))."""
         _check(lib.amgsym_lrc_setup(self._h, int(k), self._ritz_steps(k, steps), float(tol), int(seed),
                                     self._stream()))
         return self

@@ -129,8 +129,8 @@ void apply_lrc(Device* D, int32_t C, double* z, double* part, double* Hd, cudaSt
 // thick-restart Lanczos, SIAM J. Matrix Anal. Appl. 22, 2000) from the `keep`
 // Ritz vectors of the smallest Ritz values and the last Lanczos vector
 // whenever it reaches W vectors, without any special form of T.  A run ends
-// when the k smallest Ritz pairs have residuals ||X u - theta u||_B <=
-// tol * theta (|beta_W y_W| per pair).  One Krylov sequence holds a single
+// when the k smallest Ritz pairs and a buffer of max(4, k / 2) more have
+// residuals ||X u - theta u||_B <= tol * theta (|beta_W y_W| per pair).  One Krylov sequence holds a single
 // copy of a multiple eigenvalue (the mirror blocks of a cube have 3-fold
 // ones, and a correction that misses the copies barely helps), so the search
 // restarts from new random vectors kept B-orthogonal to every pair found so
@@ -145,6 +145,9 @@ struct RitzOp {
   bool b_inner = false;                                                       // B-inner product, else Euclidean
   std::function<void(const double* q, const double* bq, double* out)> apply;  // out = X q (bq = B q)
   std::function<void(const double* q, double* out)> bmul;                     // out = B q
+  // optional: picks a representative of q modulo the null space of a
+  // semi-definite B (in place), before B q and the normalisation
+  std::function<void(double* q)> project;
 };
 
 // Eigenpairs of the leading m x m part of a column's projected matrix,
@@ -188,6 +191,10 @@ void ritz_smallest(const Ctx& c, const RitzOp& op, int k, int W, double tol, uin
   const int64_t n_b = D->n_b, len = n_b * C;
   const bool bi = op.b_inner;
   const int keep = std::min(W - 2, std::max(k + 4, W / 2));
+  // pairs a run must converge: k and a buffer (max(4, k / 2)), so that an
+  // eigenvalue below the k-th one the basis has barely seen yet is not
+  // skipped when the first k pairs meet a rough tolerance
+  const int kc = std::max(k, std::min(keep - 1, k + std::max(4, k / 2)));
   const int pcap = kRitzMaxRuns * k;
   const int jmax = std::max(std::max(W + 1, pcap), std::max(n0, 1));
   DevBuf QA((int64_t)(W + 1) * len), QB((int64_t)(W + 1) * len), BQA(bi ? (int64_t)(W + 1) * len : 0),
@@ -241,6 +248,7 @@ void ritz_smallest(const Ctx& c, const RitzOp& op, int k, int W, double tol, uin
       for (auto& v : q0) v = Ud(rng);
       to_dev(w.p, q0.data(), len, st);
     }
+    if (op.project) op.project(w.p);
     norm2();
     const std::vector<double> b2_start = b2;
     for (int pass = 0; pass < 2; ++pass) {
@@ -248,6 +256,7 @@ void ritz_smallest(const Ctx& c, const RitzOp& op, int k, int W, double tol, uin
       orth_set(pool.p, bp, P);
     }
     check_launch();
+    if (op.project) op.project(w.p);
     norm2();
     std::vector<char> open(C, 0);
     bool any_open = false;
@@ -274,6 +283,7 @@ void ritz_smallest(const Ctx& c, const RitzOp& op, int k, int W, double tol, uin
         }
         check_launch();
         to_host(hh.data(), Hd.p, (int64_t)2 * (W + 1) * C, st);
+        if (op.project) op.project(w.p);
         norm2();
         for (int col = 0; col < C; ++col) {
           sv[col] = 0.0;
@@ -299,7 +309,7 @@ void ritz_smallest(const Ctx& c, const RitzOp& op, int k, int W, double tol, uin
       for (int col = 0; col < C; ++col) {
         rz[col] = col_ritz(T, W, col, valid[col]);
         const ColRitz& r = rz[col];
-        const int nk_c = std::min<int>(k, (int)r.usable.size());
+        const int nk_c = std::min<int>(kc, (int)r.usable.size());
         for (int t = 0; t < nk_c && open[col]; ++t) {
           const int e = r.usable[t];
           if (!(std::fabs(beta[col] * r.Y[(size_t)(r.m - 1) * r.m + e]) <= tol * std::fabs(r.th[e]))) conv = false;
@@ -406,6 +416,15 @@ static void lrc_setup(amgsym_t h, int32_t k, int32_t steps, double tol, uint64_t
     vcycle_apply(c, bq, out);
     check_launch();
   };
+  if (D->singular) {
+    // A^_0 is semi-definite (A^_0 1 = 0): its inner product does not see the
+    // constant, which rounding would let grow into spurious small Ritz
+    // values; vectors are kept with zero mean in block 0 (the same classes)
+    op.project = [&](double* q) {
+      launch_sub_block0_mean(q, n_b, 1, C, D->sc_out.partials, D->sc_out.partial_cap, st);
+      check_launch();
+    };
+  }
   double* U = nullptr;
   double* Vv = nullptr;
   CK(cudaMalloc(&U, sizeof(double) * (size_t)k * len));
