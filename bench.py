@@ -552,7 +552,11 @@ def run_gpu(args):
     g = gaussian_logk(N, s, seed=FIELD_SEED, corr=8.0)
     # amgr=1 also builds AMGR (Sec. 3.2) beside the I (x) M_inn hierarchy, for its variant line
     with_amgr = not args.profile_only or args.profile_only.startswith("amgr")
-    P = amg.Problem.structured(N, 1.5, g, s).setup(precisions=3, amgr=1 if with_amgr else 0)
+    extra = {}
+    for kv in args.setup_opt:  # --profile-only captures of the optional kernel forms
+        key, _, val = kv.partition("=")
+        extra[key] = type(getattr(amg.default_opts(), key))(val)
+    P = amg.Problem.structured(N, 1.5, g, s).setup(precisions=3, amgr=1 if with_amgr else 0, **extra)
     b_host = rhs_uniform(P.n, nrhs, config=3)
     b = torch.from_numpy(b_host).to(dev)
     x = torch.empty_like(b)
@@ -829,6 +833,8 @@ def main():
     ap.add_argument("--profile-grid", type=int, default=256, help="--profile-only: cells per axis")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--no-tune", action="store_true", help="batched: fixed tiles instead of the autotuner")
+    ap.add_argument("--setup-opt", action="append", default=[], metavar="KEY=VALUE",
+                    help="--profile-only: an amgsym_opts field for the setup (e.g. sell=1)")
     ap.add_argument("--profile-only", choices=["mixed", "fp64", "step", "amgr", "amgr_step"], default=None,
                     help="run one marked solve (or one profiled step) and nothing else (for ncu)")
     args = ap.parse_args()
