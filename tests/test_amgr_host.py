@@ -100,3 +100,48 @@ def test_populated_coarsening_prolongation_and_reduced_operator(N, s, bc, k):
     assert shape == Ac_ref.shape
     assert abs(Ac - Ac_ref).max() <= 1e-12 * abs(Ac_ref).max()
     assert info["levels"] >= 1
+
+
+@pytest.mark.parametrize("N,s,bc", [((12, 12, 8), 2, "neumann"), ((12, 8, 8), 3, "dirichlet"),
+                                    ((16, 12, 10), 1, "dirichlet")])
+def test_reduced_operator_is_block_diagonal_in_the_transformed_basis(N, s, bc):
+    """The identity behind the transformed-basis products of A_c (opts.amgr_sym_ac):
+    with P = I (x) P_b commuting with P_s, block (p, q) of A_c (copies p, q) is
+    2^-s sum_i s(i, p) s(i, q) A^_c,i with A^_c,i = P_b^T A^_i P_b (eq. "structAc"
+    under eq. "P_s"), and A^_c,i - P_b^T A_inn P_b is the fine interface coupling
+    A^_i - A_inn itself on the coarse indices of the interface points (they are
+    coarse, with unit rows in P_b)."""
+    from oracle import transform
+
+    g = gaussian_logk(N, s, seed=33, corr=2.0)
+    A = fv.assemble(grid.widths(N, 1.5), np.exp(g), bc)
+    perm = symmetry.mirror_perm(N, s)
+    P = amg.Problem(A.shape[0], A.indptr, A.indices, A.data, s, perm)
+    P.setup(host_only=1, amgr=1, coarse_max=64)
+    nb = 1 << s
+    H = symmetry.blocks(A, perm)
+    hat = transform.hat_blocks_sparse(H)
+    rp, ci, v, shape = P.amgr_matrix("P")
+    Pb = sp.csr_matrix((v, ci, rp), shape=shape)
+    rp, ci, v, shape = P.amgr_matrix("Ac")
+    Ac = sp.csr_matrix((v, ci, rp), shape=shape)
+    hat_c = [(Pb.T @ Ai @ Pb).tocsr() for Ai in hat]
+    scale = max(abs(Ac).max(), 1.0)
+    for p in range(nb):
+        for q in range(nb):
+            blk = Ac[p::nb][:, q::nb]
+            ref = sp.csr_matrix(blk.shape)
+            for i in range(nb):
+                ref = ref + transform.hadamard_sign(i, p) * transform.hadamard_sign(i, q) * hat_c[i]
+            ref = ref / nb
+            assert abs(blk - ref).max() <= 1e-12 * scale, (p, q)
+    # the couplings of the transformed blocks are the fine ones at coarse indices
+    cf = P.amgr_info()["cf"]
+    cidx = np.cumsum(cf == 1) - 1
+    inn_c = (Pb.T @ H[0] @ Pb).tocsr()
+    for i in range(nb):
+        fine = (hat[i] - H[0]).tocoo()
+        if fine.nnz:
+            assert np.all(cf[fine.row] == 1) and np.all(cf[fine.col] == 1)
+        ref = sp.csr_matrix((fine.data, (cidx[fine.row], cidx[fine.col])), shape=inn_c.shape)
+        assert abs((hat_c[i] - inn_c) - ref).max() <= 1e-12 * scale, i
