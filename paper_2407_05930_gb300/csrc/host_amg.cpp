@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <random>
 #include <string>
@@ -23,44 +24,129 @@
 
 namespace amgsym {
 
+// Sorts the entries e in [b, e) of A by column, through the scratch tmp.
+static void sort_range(Csr& A, int64_t b, int64_t e, std::vector<std::pair<int32_t, double>>& tmp) {
+  tmp.resize(e - b);
+  for (int64_t k = b; k < e; ++k) tmp[k - b] = {A.idx[k], A.val[k]};
+  std::sort(tmp.begin(), tmp.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+  for (int64_t k = b; k < e; ++k) {
+    A.idx[k] = tmp[k - b].first;
+    A.val[k] = tmp[k - b].second;
+  }
+}
+
 void sort_rows(Csr& A) {
-#pragma omp parallel for schedule(dynamic, 1024)
-  for (int64_t i = 0; i < A.rows; ++i) {
-    const int64_t b = A.ptr[i], e = A.ptr[i + 1];
-    bool sorted = true;
-    for (int64_t k = b + 1; k < e; ++k)
-      if (A.idx[k] < A.idx[k - 1]) {
-        sorted = false;
-        break;
-      }
-    if (sorted) continue;
-    std::vector<std::pair<int32_t, double>> tmp(e - b);
-    for (int64_t k = b; k < e; ++k) tmp[k - b] = {A.idx[k], A.val[k]};
-    std::sort(tmp.begin(), tmp.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-    for (int64_t k = b; k < e; ++k) {
-      A.idx[k] = tmp[k - b].first;
-      A.val[k] = tmp[k - b].second;
+#pragma omp parallel
+  {
+    std::vector<std::pair<int32_t, double>> tmp;
+#pragma omp for schedule(dynamic, 1024)
+    for (int64_t i = 0; i < A.rows; ++i) {
+      const int64_t b = A.ptr[i], e = A.ptr[i + 1];
+      bool sorted = true;
+      for (int64_t k = b + 1; k < e; ++k)
+        if (A.idx[k] < A.idx[k - 1]) {
+          sorted = false;
+          break;
+        }
+      if (!sorted) sort_range(A, b, e, tmp);
     }
   }
 }
 
+static int host_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// Rows of T = A^T come out in ascending source-row order.  Large matrices
+// are split into contiguous chunks of source rows: each chunk counts its
+// entries per column, a column's slots are handed out chunk after chunk,
+// and each chunk fills its slots in row order, which gives the same arrays
+// as one sequential pass.
 Csr transpose(const Csr& A) {
   Csr T;
   T.rows = A.cols;
   T.cols = A.rows;
   T.ptr.assign(T.rows + 1, 0);
-  for (int64_t e = 0; e < A.nnz(); ++e) T.ptr[A.idx[e] + 1]++;
-  for (int64_t i = 0; i < T.rows; ++i) T.ptr[i + 1] += T.ptr[i];
-  T.idx.resize(A.nnz());
-  T.val.resize(A.nnz());
-  std::vector<int64_t> fill(T.ptr.begin(), T.ptr.end() - 1);
-  for (int64_t i = 0; i < A.rows; ++i)
-    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
-      const int64_t k = fill[A.idx[e]]++;
-      T.idx[k] = (int32_t)i;
-      T.val[k] = A.val[e];
+  const int64_t nnz = A.nnz();
+  T.idx.resize(nnz);
+  T.val.resize(nnz);
+  const int64_t nch = nnz < (int64_t)1 << 20 ? 1 : std::min<int64_t>(std::min(host_threads(), 16), A.rows);
+  if (nch <= 1) {
+    for (int64_t e = 0; e < nnz; ++e) T.ptr[A.idx[e] + 1]++;
+    for (int64_t i = 0; i < T.rows; ++i) T.ptr[i + 1] += T.ptr[i];
+    std::vector<int64_t> fill(T.ptr.begin(), T.ptr.end() - 1);
+    for (int64_t i = 0; i < A.rows; ++i)
+      for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+        const int64_t k = fill[A.idx[e]]++;
+        T.idx[k] = (int32_t)i;
+        T.val[k] = A.val[e];
+      }
+    return T;
+  }
+  const int64_t nc = T.rows;
+  // cnt[k * nc + c]: entries of chunk k in column c, then that chunk's first
+  // slot within the column (a column holds < 2^31 entries: int32 indices)
+  std::unique_ptr<int32_t[]> cnt(new int32_t[(size_t)(nch * nc)]);
+  auto row0 = [&](int64_t k) { return A.rows * k / nch; };
+#pragma omp parallel for schedule(static, 1)
+  for (int64_t k = 0; k < nch; ++k) {
+    int32_t* ck = cnt.get() + k * nc;
+    std::fill(ck, ck + nc, 0);
+    for (int64_t e = A.ptr[row0(k)]; e < A.ptr[row0(k + 1)]; ++e) ck[A.idx[e]]++;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nc; ++c) {
+    int32_t run = 0;
+    for (int64_t k = 0; k < nch; ++k) {
+      const int32_t v = cnt[k * nc + c];
+      cnt[k * nc + c] = run;
+      run += v;
     }
+    T.ptr[c + 1] = run;
+  }
+  for (int64_t c = 0; c < nc; ++c) T.ptr[c + 1] += T.ptr[c];
+#pragma omp parallel for schedule(static, 1)
+  for (int64_t k = 0; k < nch; ++k) {
+    int32_t* ck = cnt.get() + k * nc;
+    for (int64_t i = row0(k); i < row0(k + 1); ++i)
+      for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+        const int32_t c = A.idx[e];
+        const int64_t slot = T.ptr[c] + ck[c]++;
+        T.idx[slot] = (int32_t)i;
+        T.val[slot] = A.val[e];
+      }
+  }
   return T;
+}
+
+// The entries e of A with keep[e] set, as a pattern (unit values), rows in
+// A's order.
+Csr pattern_of(const Csr& A, const std::vector<uint8_t>& keep) {
+  const int64_t n = A.rows;
+  Csr S;
+  S.rows = n;
+  S.cols = A.cols;
+  S.ptr.assign(n + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = 0;
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) c += keep[e] != 0;
+    S.ptr[i + 1] = c;
+  }
+  for (int64_t i = 0; i < n; ++i) S.ptr[i + 1] += S.ptr[i];
+  S.idx.resize(S.ptr[n]);
+  S.val.assign(S.ptr[n], 1.0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t w = S.ptr[i];
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e)
+      if (keep[e]) S.idx[w++] = A.idx[e];
+  }
+  return S;
 }
 
 // C = A B (Gustavson, two passes, rows sorted, exact zeros kept out only if
@@ -95,6 +181,7 @@ Csr spgemm(const Csr& A, const Csr& B) {
 #pragma omp parallel
   {
     std::vector<int64_t> pos(B.cols, -1);
+    std::vector<std::pair<int32_t, double>> tmp;
 #pragma omp for schedule(dynamic, 512)
     for (int64_t i = 0; i < A.rows; ++i) {
       int64_t w = C.ptr[i];
@@ -114,14 +201,7 @@ Csr spgemm(const Csr& A, const Csr& B) {
           }
         }
       }
-      // sort the row
-      std::vector<std::pair<int32_t, double>> tmp(w - start);
-      for (int64_t k = start; k < w; ++k) tmp[k - start] = {C.idx[k], C.val[k]};
-      std::sort(tmp.begin(), tmp.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
-      for (int64_t k = start; k < w; ++k) {
-        C.idx[k] = tmp[k - start].first;
-        C.val[k] = tmp[k - start].second;
-      }
+      sort_range(C, start, w, tmp);
     }
   }
   return C;
@@ -162,22 +242,9 @@ std::vector<uint8_t> strength(const Csr& A, double theta) {
 // PMIS coarsening (De Sterck, Yang, Heys 2006): cf[i] = 1 (C) or -1 (F).
 static std::vector<int8_t> pmis(const Csr& A, const std::vector<uint8_t>& strong, uint64_t seed) {
   const int64_t n = A.rows;
-  // S^T: for each i, the j that strongly depend on i.
-  Csr S;
-  S.rows = S.cols = n;
-  S.ptr.assign(n + 1, 0);
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e)
-      if (strong[e]) S.ptr[i + 1]++;
-  for (int64_t i = 0; i < n; ++i) S.ptr[i + 1] += S.ptr[i];
-  S.idx.resize(S.ptr[n]);
-  S.val.assign(S.ptr[n], 1.0);
-  {
-    int64_t w = 0;
-    for (int64_t i = 0; i < n; ++i)
-      for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e)
-        if (strong[e]) S.idx[w++] = A.idx[e];
-  }
+  // S: for each i, the j that i strongly depends on; S^T: the j that
+  // strongly depend on i.
+  Csr S = pattern_of(A, strong);
   Csr ST = transpose(S);
   std::vector<double> measure(n);
   std::mt19937_64 rng(seed);
@@ -185,6 +252,7 @@ static std::vector<int8_t> pmis(const Csr& A, const std::vector<uint8_t>& strong
   for (int64_t i = 0; i < n; ++i) measure[i] = (double)(ST.ptr[i + 1] - ST.ptr[i]) + U(rng);
   std::vector<int8_t> cf(n, 0);
   int64_t undecided = 0;
+#pragma omp parallel for schedule(static) reduction(+ : undecided)
   for (int64_t i = 0; i < n; ++i) {
     if (ST.ptr[i + 1] == ST.ptr[i]) cf[i] = -1;  // influences nobody
     else ++undecided;
@@ -207,21 +275,48 @@ static std::vector<int8_t> pmis(const Csr& A, const std::vector<uint8_t>& strong
       }
       newc[i] = best ? 1 : 0;
     }
-    for (int64_t i = 0; i < n; ++i)
-      if (newc[i]) cf[i] = 1;
-    for (int64_t i = 0; i < n; ++i)
-      if (newc[i])
-        for (int64_t e = ST.ptr[i]; e < ST.ptr[i + 1]; ++e) {
-          const int32_t j = ST.idx[e];
-          if (cf[j] == 0) cf[j] = -1;
-        }
+    // the new C points; every other undecided point that strongly depends
+    // on one of them (a new C point in its row of S) becomes F
     undecided = 0;
-    for (int64_t i = 0; i < n; ++i)
-      if (cf[i] == 0) ++undecided;
+#pragma omp parallel for schedule(static) reduction(+ : undecided)
+    for (int64_t i = 0; i < n; ++i) {
+      if (cf[i] != 0) continue;
+      if (newc[i]) {
+        cf[i] = 1;
+        continue;
+      }
+      bool f = false;
+      for (int64_t e = S.ptr[i]; e < S.ptr[i + 1] && !f; ++e) f = newc[S.idx[e]] != 0;
+      if (f) cf[i] = -1;
+      else ++undecided;
+    }
   }
   for (int64_t i = 0; i < n; ++i)
     if (cf[i] == 0) cf[i] = 1;
   return cf;
+}
+
+// CSR from per-row lists of (column, value), in list order; the lists are
+// released as they are copied.
+static Csr from_rows(int64_t cols, std::vector<std::vector<std::pair<int32_t, double>>>& rows) {
+  const int64_t n = (int64_t)rows.size();
+  Csr M;
+  M.rows = n;
+  M.cols = cols;
+  M.ptr.assign(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) M.ptr[i + 1] = M.ptr[i] + (int64_t)rows[i].size();
+  M.idx.resize(M.ptr[n]);
+  M.val.resize(M.ptr[n]);
+#pragma omp parallel for schedule(static, 4096)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t w = M.ptr[i];
+    for (const auto& p : rows[i]) {
+      M.idx[w] = p.first;
+      M.val[w++] = p.second;
+    }
+    std::vector<std::pair<int32_t, double>>().swap(rows[i]);
+  }
+  return M;
 }
 
 // Extended+i interpolation (De Sterck, Falgout, Nolting, Yang 2008) with
@@ -235,6 +330,7 @@ Csr ext_i_interp(const Csr& A, const std::vector<uint8_t>& strong,
   for (int64_t i = 0; i < n; ++i)
     if (cf[i] > 0) cmap[i] = nc++;
   std::vector<double> diag(n);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) diag[i] = find(A, i, (int32_t)i);
   std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
 #pragma omp parallel
@@ -329,21 +425,7 @@ Csr ext_i_interp(const Csr& A, const std::vector<uint8_t>& strong,
       std::sort(out.begin(), out.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
     }
   }
-  Csr P;
-  P.rows = n;
-  P.cols = nc;
-  P.ptr.assign(n + 1, 0);
-  for (int64_t i = 0; i < n; ++i) P.ptr[i + 1] = P.ptr[i] + (int64_t)rows[i].size();
-  P.idx.resize(P.ptr[n]);
-  P.val.resize(P.ptr[n]);
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t w = P.ptr[i];
-    for (auto& p : rows[i]) {
-      P.idx[w] = p.first;
-      P.val[w++] = p.second;
-    }
-  }
-  return P;
+  return from_rows(nc, rows);
 }
 
 // Small dense Cholesky solve A y = rhs in place (m x m, row-major); false if
@@ -415,20 +497,7 @@ Csr fsai(const Csr& A, int max_lower) {
       }
     }
   }
-  Csr G;
-  G.rows = G.cols = n;
-  G.ptr.assign(n + 1, 0);
-  for (int64_t i = 0; i < n; ++i) G.ptr[i + 1] = G.ptr[i] + (int64_t)rows[i].size();
-  G.idx.resize(G.ptr[n]);
-  G.val.resize(G.ptr[n]);
-  for (int64_t i = 0; i < n; ++i) {
-    int64_t w = G.ptr[i];
-    for (auto& p : rows[i]) {
-      G.idx[w] = p.first;
-      G.val[w++] = p.second;
-    }
-  }
-  return G;
+  return from_rows(n, rows);
 }
 
 // Largest eigenvalue of G A G^T by power iteration (an estimate from below;
@@ -534,12 +603,14 @@ static Csr sparsify(const Csr& A, double theta) {
   if (theta <= 0.0) return A;
   const int64_t n = A.rows;
   std::vector<double> diag(n, 0.0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) diag[i] = find(A, i, (int32_t)i);
   Csr B;
   B.rows = A.rows;
   B.cols = A.cols;
   B.ptr.assign(n + 1, 0);
   std::vector<double> lump(n, 0.0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     int64_t cnt = 0;
     for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
@@ -550,10 +621,12 @@ static Csr sparsify(const Csr& A, double theta) {
       else
         lump[i] += A.val[e];
     }
-    B.ptr[i + 1] = B.ptr[i] + cnt;
+    B.ptr[i + 1] = cnt;
   }
+  for (int64_t i = 0; i < n; ++i) B.ptr[i + 1] += B.ptr[i];
   B.idx.resize(B.ptr[n]);
   B.val.resize(B.ptr[n]);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     int64_t w = B.ptr[i];
     for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
@@ -571,20 +644,41 @@ static Csr sparsify(const Csr& A, double theta) {
   return B;
 }
 
-// (A + A^T) / 2 for a matrix with a symmetric pattern and sorted rows (the
-// Galerkin product is symmetric up to rounding); unchanged otherwise.
+// (A + A^T) / 2 for a matrix with a symmetric pattern and sorted rows
+// without repeated columns (the Galerkin product: symmetric up to rounding);
+// unchanged otherwise.  Each pair (i, j), (j, i) with j < i gets the mean of
+// its two values; a diagonal entry stays as it is.
 static void symmetrize(Csr& A) {
-  Csr T = transpose(A);
-  if (T.ptr != A.ptr || T.idx != A.idx) return;
-  for (int64_t e = 0; e < A.nnz(); ++e) A.val[e] = 0.5 * (A.val[e] + T.val[e]);
+  const int64_t n = A.rows;
+  if (A.cols != n) return;
+  // the position of (j, i), or -1
+  auto mirror = [&](int64_t i, int32_t j) -> int64_t {
+    const int32_t* b = A.idx.data() + A.ptr[j];
+    const int32_t* f = A.idx.data() + A.ptr[j + 1];
+    const int32_t* it = std::lower_bound(b, f, (int32_t)i);
+    return (it != f && *it == i) ? it - A.idx.data() : -1;
+  };
+  int64_t missing = 0;
+#pragma omp parallel for schedule(static) reduction(+ : missing)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) missing += mirror(i, A.idx[e]) < 0;
+  if (missing) return;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1] && A.idx[e] < i; ++e) {
+      const int64_t f = mirror(i, A.idx[e]);
+      const double v = 0.5 * (A.val[e] + A.val[f]);
+      A.val[e] = v;
+      A.val[f] = v;
+    }
 }
 
 static constexpr int64_t kDenseLimit = 4096;
 
-void build_hierarchy(const Csr& A0, const amgsym_opts& o, HostHierarchy& H) {
+void build_hierarchy(Csr A0, const amgsym_opts& o, HostHierarchy& H) {
   H.levels.clear();
   H.levels.emplace_back();
-  H.levels[0].A = A0;
+  H.levels[0].A = std::move(A0);
   sort_rows(H.levels[0].A);
   for (int lev = 0;; ++lev) {
     HostLevel& L = H.levels[lev];

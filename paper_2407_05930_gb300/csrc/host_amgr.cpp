@@ -43,21 +43,11 @@ static std::vector<uint8_t> mis_distance(const Csr& A, const std::vector<uint8_t
                                          const std::vector<uint8_t>& inner, int dist, uint64_t seed) {
   const int64_t n = A.rows;
   // T = strong pattern symmetrised, inner points only
-  Csr S;
-  S.rows = S.cols = n;
-  S.ptr.assign(n + 1, 0);
+  std::vector<uint8_t> keep(A.nnz(), 0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i)
-    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e)
-      if (strong[e] && inner[i] && inner[A.idx[e]]) S.ptr[i + 1]++;
-  for (int64_t i = 0; i < n; ++i) S.ptr[i + 1] += S.ptr[i];
-  S.idx.resize(S.ptr[n]);
-  S.val.assign(S.ptr[n], 1.0);
-  {
-    int64_t w = 0;
-    for (int64_t i = 0; i < n; ++i)
-      for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e)
-        if (strong[e] && inner[i] && inner[A.idx[e]]) S.idx[w++] = A.idx[e];
-  }
+    for (int64_t e = A.ptr[i]; e < A.ptr[i + 1]; ++e) keep[e] = strong[e] && inner[i] && inner[A.idx[e]];
+  const Csr S = pattern_of(A, keep);
   const Csr ST = transpose(S);
   std::vector<int64_t> order;
   for (int64_t i = 0; i < n; ++i)
@@ -101,6 +91,7 @@ static double lambda_max_diag_scaled(const Csr& A, const std::vector<int64_t>& r
   std::vector<int64_t> pos(A.rows, -1);
   for (int64_t k = 0; k < m; ++k) pos[rows[k]] = k;
   std::vector<double> dinv(m), v(m), w(m);
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < m; ++k) {
     double d = 0.0;
     for (int64_t e = A.ptr[rows[k]]; e < A.ptr[rows[k] + 1]; ++e)
@@ -117,6 +108,7 @@ static double lambda_max_diag_scaled(const Csr& A, const std::vector<int64_t>& r
     nv = std::sqrt(nv);
     if (nv == 0.0) break;
     for (auto& x : v) x /= nv;
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < m; ++k) {
       double s = 0.0;
       const int64_t r = rows[k];
@@ -239,39 +231,51 @@ void build_amgr(amgsym_problem* p, const amgsym_opts& o) {
       if (hm != 0.0) cross[rc].push_back({cc, m, hm});
     }
   }
+  // row (lc, j) of A_c: row lc of Ac0 in copy j, then the couplings to the
+  // copies j XOR m (no column repeats: those land in other copies)
   const int64_t nc = (int64_t)H->n_cb * nb;
-  Csr& Ac = H->Ac;
+  Csr Ac;
   Ac.rows = Ac.cols = nc;
   Ac.ptr.assign(nc + 1, 0);
-  for (int64_t lc = 0; lc < H->n_cb; ++lc)
-    for (int32_t j = 0; j < nb; ++j) {
-      for (int64_t e = Ac0.ptr[lc]; e < Ac0.ptr[lc + 1]; ++e) {
-        Ac.idx.push_back(Ac0.idx[e] * nb + j);
-        Ac.val.push_back(Ac0.val[e]);
-      }
-      for (const auto& t : cross[lc]) {
-        Ac.idx.push_back(std::get<0>(t) * nb + (j ^ std::get<1>(t)));
-        Ac.val.push_back(std::get<2>(t));
-      }
-      Ac.ptr[lc * nb + j + 1] = (int64_t)Ac.idx.size();
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nc; ++r) {
+    const int64_t lc = r / nb;
+    Ac.ptr[r + 1] = (Ac0.ptr[lc + 1] - Ac0.ptr[lc]) + (int64_t)cross[lc].size();
+  }
+  for (int64_t r = 0; r < nc; ++r) Ac.ptr[r + 1] += Ac.ptr[r];
+  Ac.idx.resize(Ac.ptr[nc]);
+  Ac.val.resize(Ac.ptr[nc]);
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nc; ++r) {
+    const int64_t lc = r / nb;
+    const int32_t j = (int32_t)(r % nb);
+    int64_t w = Ac.ptr[r];
+    for (int64_t e = Ac0.ptr[lc]; e < Ac0.ptr[lc + 1]; ++e) {
+      Ac.idx[w] = Ac0.idx[e] * nb + j;
+      Ac.val[w++] = Ac0.val[e];
     }
+    for (const auto& t : cross[lc]) {
+      Ac.idx[w] = std::get<0>(t) * nb + (j ^ std::get<1>(t));
+      Ac.val[w++] = std::get<2>(t);
+    }
+  }
   sort_rows(Ac);
   H->Ac0 = std::move(Ac0);
-  // merge duplicate columns (none expected: H_m of distinct m land in distinct copies)
-  // the coarse problem: s = 0, its own standard AMG hierarchy
+  // the coarse problem: s = 0, its own standard AMG hierarchy, whose finest
+  // level takes over A_c (its Ainn keeps only the shape)
   auto* cp = new amgsym_problem();
   cp->n = nc;
   cp->n_b = nc;
   cp->s = 0;
   cp->nb = 1;
-  cp->Ainn = Ac;
+  cp->Ainn.rows = cp->Ainn.cols = nc;
   cp->perm.resize(nc);
   std::iota(cp->perm.begin(), cp->perm.end(), 0);
   cp->singular = p->singular;
   cp->opts = o;
   cp->opts.amgr = 0;
   cp->opts.dia_max_diag = 0;
-  build_hierarchy(cp->Ainn, cp->opts, cp->H);
+  build_hierarchy(std::move(Ac), cp->opts, cp->H);
   cp->have_hierarchy = true;
   H->coarse = std::shared_ptr<amgsym_problem>(cp, [](amgsym_problem* q) { amgsym_destroy(q); });
   p->amgr = H;

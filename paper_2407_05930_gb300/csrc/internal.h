@@ -78,14 +78,15 @@ struct HostAmgr {
   Csr GK, GKt;              // FSAI of K = A_inn[F, F], embedded in n_b x n_b (fine rows and columns)
   double omegaK = 1.0;      // damping of the fine-point smoother
   std::vector<double> jdC;  // coarse rows: omega_C / a_ll (the FSAI of C-bar with a diagonal pattern); fine rows 0
-  Csr Ac;                   // full reduced operator, n_cb * 2^s rows, copy index fastest
   // A_c in the transformed basis (eq. "structAc" under P_s): block i is
   // Ac0 + the interface couplings of block i, Ac0 = P_b^T A_inn P_b; the
   // couplings are the fine ones (ivals, [entry][block]) at coarse indices
   Csr Ac0;
   std::vector<int32_t> cirow, cicol;
   std::vector<double> civals;
-  std::shared_ptr<amgsym_problem> coarse;  // Ac with its AMG hierarchy (and device copies)
+  // the full reduced operator A_c (n_cb * 2^s rows, copy index fastest) as
+  // the finest level of its own AMG hierarchy (and device copies)
+  std::shared_ptr<amgsym_problem> coarse;
 };
 
 }  // namespace amgsym
@@ -115,7 +116,8 @@ struct amgsym_problem {
 
 namespace amgsym {
 // host_amg.cpp
-void build_hierarchy(const Csr& A, const amgsym_opts& o, HostHierarchy& H);
+// the hierarchy of A (taken by value: pass an rvalue to hand the matrix over)
+void build_hierarchy(Csr A, const amgsym_opts& o, HostHierarchy& H);
 // classical strength: strong[e] = 1 when -a_ij >= theta max_k (-a_ik) (entry e = (i, j))
 std::vector<uint8_t> strength(const Csr& A, double theta);
 // extended+i interpolation for the splitting cf (1 = C, -1 = F), truncated
@@ -128,6 +130,8 @@ double lambda_max_GAGt(const Csr& A, const Csr& G, const Csr& Gt, uint64_t seed)
 // host_amgr.cpp
 void build_amgr(amgsym_problem* p, const amgsym_opts& o);
 Csr transpose(const Csr& A);
+// the entries e with keep[e] != 0, unit values
+Csr pattern_of(const Csr& A, const std::vector<uint8_t>& keep);
 Csr spgemm(const Csr& A, const Csr& B);
 void sort_rows(Csr& A);
 // solve.cu

@@ -1658,7 +1658,7 @@ extern "C" amgsym_status amgsym_amgr_info(amgsym_t h, int64_t* n_coarse_per_copy
   const HostAmgr& M = *h->amgr;
   if (n_coarse_per_copy) *n_coarse_per_copy = M.n_cb;
   if (nnz_P) *nnz_P = M.Pb.nnz();
-  if (nnz_Ac) *nnz_Ac = M.Ac.nnz();
+  if (nnz_Ac) *nnz_Ac = M.coarse->H.levels[0].A.nnz();
   if (coarse_levels) *coarse_levels = (int32_t)M.coarse->H.levels.size();
   if (cf) std::memcpy(cf, M.cf.data(), M.cf.size());
   API_END
@@ -1670,7 +1670,7 @@ extern "C" amgsym_status amgsym_amgr_matrix(amgsym_t h, int32_t which, int64_t* 
   if (!h || !rowptr || !colidx || !vals) fail(AMGSYM_ERR_ARG, "NULL argument");
   if (!h->amgr) fail(AMGSYM_ERR_STATE, "AMGR was not built: call amgsym_setup with opts.amgr = 1");
   if (which != 0 && which != 1) fail(AMGSYM_ERR_ARG, "which must be 0 (P_b) or 1 (A_c)");
-  const Csr& M = which == 0 ? h->amgr->Pb : h->amgr->Ac;
+  const Csr& M = which == 0 ? h->amgr->Pb : h->amgr->coarse->H.levels[0].A;
   std::memcpy(rowptr, M.ptr.data(), sizeof(int64_t) * M.ptr.size());
   std::memcpy(colidx, M.idx.data(), sizeof(int32_t) * M.idx.size());
   std::memcpy(vals, M.val.data(), sizeof(double) * M.val.size());

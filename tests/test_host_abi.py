@@ -157,6 +157,8 @@ def test_hierarchy_structure(drop):
         # Galerkin coarse operator R A P with R = P^T; sparsified: small
         # couplings moved to the diagonal (row sums and symmetry kept)
         ref = (Pm.T @ A @ Pm).tocsr()
+        # symmetrised exactly: each pair (i, j), (j, i) holds one value
+        assert (Ac != Ac.T).nnz == 0
         if drop == 0.0:
             assert abs(Ac - ref).max() <= 1e-12 * abs(ref).max()
         else:
