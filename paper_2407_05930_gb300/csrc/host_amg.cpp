@@ -338,6 +338,7 @@ Csr ext_i_interp(const Csr& A, const std::vector<uint8_t>& strong,
     std::vector<int64_t> mark(n, -1);  // mark[j] == i  <=> j in C^_i
     std::vector<double> num(n, 0.0);
     std::vector<int32_t> chat;
+    std::vector<std::pair<int32_t, double>> w;
 #pragma omp for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
       auto& out = rows[i];
@@ -402,8 +403,7 @@ Csr ext_i_interp(const Csr& A, const std::vector<uint8_t>& strong,
         }
       }
       if (dt == 0.0) continue;
-      std::vector<std::pair<int32_t, double>> w;
-      w.reserve(chat.size());
+      w.clear();
       double sum_all = 0.0;
       for (int32_t j : chat) {
         const double wij = -num[j] / dt;
