@@ -74,7 +74,10 @@ Csr transpose(const Csr& A) {
   const int64_t nnz = A.nnz();
   T.idx.resize(nnz);
   T.val.resize(nnz);
-  const int64_t nch = nnz < (int64_t)1 << 20 ? 1 : std::min<int64_t>(std::min(host_threads(), 16), A.rows);
+  // chunks: one per thread (at most 16), with the 4-byte column counters of
+  // all chunks at most half the 12 bytes per entry of the matrix
+  int64_t nch = nnz < (int64_t)1 << 20 ? 1 : std::min<int64_t>(std::min(host_threads(), 16), A.rows);
+  nch = std::min<int64_t>(nch, std::max<int64_t>(1, 3 * nnz / (2 * std::max<int64_t>(A.cols, 1))));
   if (nch <= 1) {
     for (int64_t e = 0; e < nnz; ++e) T.ptr[A.idx[e] + 1]++;
     for (int64_t i = 0; i < T.rows; ++i) T.ptr[i + 1] += T.ptr[i];
