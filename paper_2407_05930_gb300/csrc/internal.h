@@ -96,7 +96,8 @@ struct amgsym_problem {
   int64_t n_b = 0;    // base-block rows, n / 2^s
   int32_t s = 0;
   int32_t nb = 1;     // 2^s
-  amgsym::Csr Ainn;   // H_0, columns sorted
+  amgsym::Csr Ainn;   // H_0, columns sorted (AMGR's coarse problem: the shape only; its
+                      // matrix is the finest level of its hierarchy)
   // Interface couplings: entries sorted by (row, col); ivals[e * nb + i] =
   // (A_out,i)[row, col].
   std::vector<int32_t> irow, icol;
